@@ -1,0 +1,799 @@
+/*
+ * oecdg_oracle.c -- plain, slow FP64 CPU oracle of the OECDG scheme
+ * (Peng, Wu, Yuan, "Oscillation-eliminating central DG schemes for hyperbolic
+ * conservation laws", arXiv:2503.12473).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file exists to check the CUDA path.  It is
+ * called from the test-suite, from the package's smoke() entry and from the
+ * benchmark's CPU-baseline leg; nothing in the product path may link or call it.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Every quantity is computed the literal way the paper defines it:
+ *   - the CDG operator H (Section 2.1, Eq. (equcdg) / 1D Eq. (eq:1D_H) /
+ *     2D Eq. (eq:2D_H)) by Gauss quadrature on the sub-cells cut by the
+ *     overlapping mesh and on the half-faces, locating the overlapping cell of
+ *     every quadrature point from its physical coordinates and evaluating both
+ *     Legendre expansions directly at that point;
+ *   - the damping coefficients delta_K^m, sigma_K and beta_{e,K} (Section 2.2,
+ *     the definitions that follow Eq. (OEstep2D), and the two Remarks on 1D and
+ *     on systems);
+ *   - the exact solution of the damping ODE (OEstep2D) in the orthogonal
+ *     Legendre basis (the coefficients decay exponentially, Section 3.3);
+ *   - the fully discrete RK scheme (Eq. (eq:RKCDG)) with the Shu-Osher forms of
+ *     forward Euler, SSP-RK2, SSP-RK3 and classical RK4 (Section 4).
+ *
+ * Readings of points the paper leaves open (the CUDA path implements the same
+ * readings independently):
+ *   - the dual mesh is the primal mesh shifted by (+hx/2, +hy/2), with the same
+ *     number of cells; transmissive boundaries: a ghost cell outside the stored
+ *     range is a copy of the nearest stored cell (all modes), per direction;
+ *   - quadrature: (k+1)-point Gauss-Legendre per direction on every sub-cell and
+ *     half-face; Legendre polynomials unnormalised (P_n(1) = 1);
+ *   - tau_max is the CFL value at the start of the step (maximum wave speed over
+ *     the cell averages of both meshes), tau = tau_max except a final clipped step;
+ *   - sigma: max over the (k+1)^d cell Gauss points, avg over stored cells;
+ *   - h_{e,K} = the cell width normal to e; Sum_{|alpha|=m} is the plain
+ *     multi-index sum; beta_{e,K} at K's cell average;
+ *   - Q^k cells: P^{m-1} is the total-degree projection, so mode (a,b) decays at
+ *     rate Sum_{m=0}^{min(a+b,k)} delta^m;
+ *   - the OE time is the full step tau after every stage; OE is off for k = 0.
+ *
+ * Every function whose result has no independent pin in tests/ says
+ * "parity unpinned" in its comment.
+ *
+ * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -shared -fPIC
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXK 3
+#define ORC_MAXQ (ORC_MAXK + 1)
+#define ORC_MAXF 4
+#define ORC_MAXM ((ORC_MAXK + 1) * (ORC_MAXK + 1))
+
+enum { ORC_ADVECTION = 0, ORC_BURGERS = 1, ORC_EULER = 2 };
+enum { ORC_BASIS_Q = 0, ORC_BASIS_P = 1 };
+enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1 };
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENONPHYSICAL = 4 };
+
+/* Problem description (mirrored by a ctypes.Structure in oracle/oracle.py). */
+typedef struct {
+  int dim;     /* 1 or 2 */
+  int nx, ny;  /* primal cells per direction (ny = 1 when dim = 1) */
+  int k;       /* polynomial degree, 0..3 */
+  int basis;   /* ORC_BASIS_Q (tensor Q^k) or ORC_BASIS_P (total degree P^k) */
+  int system;  /* ORC_ADVECTION, ORC_BURGERS, ORC_EULER */
+  int bc;      /* ORC_PERIODIC or ORC_TRANSMISSIVE (same on every side) */
+  int oe;      /* 1: apply the OE step after every stage */
+  int rk;      /* 1 forward Euler, 2 SSP-RK2, 3 SSP-RK3, 4 classical RK4 */
+  int pad;
+  double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
+  double gamma;          /* ratio of specific heats (Euler) */
+  double adv_x, adv_y;   /* advection velocity */
+  double cfl;            /* C_CFL */
+} orc_problem;
+
+/* ---------------------------------------------------------------- basics -- */
+
+static int nfields(const orc_problem* p) {
+  return p->system == ORC_EULER ? p->dim + 2 : 1;
+}
+
+/* Mode list: (a, b) degrees in x and y.  Q^k: index b*(k+1)+a.  P^k: ordered
+ * by total degree s = a+b, then by decreasing a.  1D: (a, 0), a = 0..k. */
+static int modes(const orc_problem* p, int* ma, int* mb) {
+  int k = p->k, n = 0;
+  if (p->dim == 1) {
+    for (int a = 0; a <= k; ++a) { ma[n] = a; mb[n] = 0; ++n; }
+  } else if (p->basis == ORC_BASIS_Q) {
+    for (int b = 0; b <= k; ++b)
+      for (int a = 0; a <= k; ++a) { ma[n] = a; mb[n] = b; ++n; }
+  } else {
+    for (int s = 0; s <= k; ++s)
+      for (int a = s; a >= 0; --a) { ma[n] = a; mb[n] = s - a; ++n; }
+  }
+  return n;
+}
+
+static int nmodes(const orc_problem* p) {
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  return modes(p, ma, mb);
+}
+
+static double hx_of(const orc_problem* p) { return (p->bx - p->ax) / p->nx; }
+static double hy_of(const orc_problem* p) { return p->dim == 2 ? (p->by - p->ay) / p->ny : 1.0; }
+
+/* Index of coefficient (mesh, field, mode, j, i) in the state array. */
+static size_t sidx(const orc_problem* p, int mesh, int f, int m, int j, int i) {
+  int F = nfields(p), M = nmodes(p);
+  return ((((size_t)mesh * F + f) * M + m) * p->ny + j) * (size_t)p->nx + i;
+}
+
+/* d-th derivative of the Legendre polynomial P_n at x (unnormalised, P_n(1)=1).
+ * Three-term recurrence for the values and P^{(d)}_{n+1} = P^{(d)}_{n-1} +
+ * (2n+1) P^{(d-1)}_n for the derivatives. */
+double orc_legendre(int n, int d, double x) {
+  double t[ORC_MAXK + 3][ORC_MAXK + 3];
+  int N = n + 1;
+  memset(t, 0, sizeof t);
+  t[0][0] = 1.0;
+  if (N > 1) t[0][1] = x;
+  for (int q = 1; q + 1 < N; ++q) t[0][q + 1] = ((2.0 * q + 1.0) * x * t[0][q] - q * t[0][q - 1]) / (q + 1.0);
+  for (int e = 1; e <= d; ++e) {
+    t[e][0] = 0.0;
+    if (N > 1) t[e][1] = (e == 1) ? 1.0 : 0.0;
+    for (int q = 1; q + 1 < N; ++q) t[e][q + 1] = t[e][q - 1] + (2.0 * q + 1.0) * t[e - 1][q];
+  }
+  return t[d][n];
+}
+
+/* n-point Gauss-Legendre rule on [-1,1]: Newton iteration on P_n started from
+ * the asymptotic root guesses; weights 2 / ((1 - x^2) P_n'(x)^2). */
+void orc_gauss(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double dz = orc_legendre(n, 0, z) / orc_legendre(n, 1, z);
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    double d1 = orc_legendre(n, 1, z);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * d1 * d1);
+  }
+}
+
+/* Centre of cell (i, j) of mesh `mesh` (0 primal, 1 dual).  The dual mesh is
+ * the primal mesh shifted by (+hx/2, +hy/2) (Section 2.1): dual cell i spans
+ * [x_i, x_{i+1}] between primal centres, i.e. it is centred on primal vertex i+1. */
+static void cell_centre(const orc_problem* p, int mesh, int i, int j, double* xc, double* yc) {
+  double hx = hx_of(p), hy = hy_of(p);
+  *xc = p->ax + (i + 0.5 + 0.5 * mesh) * hx;
+  *yc = p->dim == 2 ? p->ay + (j + 0.5 + 0.5 * mesh) * hy : 0.0;
+}
+
+/* Map an unwrapped cell index to a stored one: periodic wrap, or the
+ * transmissive ghost convention (ghost cell := copy of the nearest stored cell,
+ * every mode copied; corners by composition).  The paper does not say how the
+ * dual mesh is closed at an outflow boundary: the transmissive branch is a
+ * convention, parity unpinned. */
+static int store_index(const orc_problem* p, int iu, int n) {
+  if (p->bc == ORC_PERIODIC) return ((iu % n) + n) % n;
+  return iu < 0 ? 0 : (iu >= n ? n - 1 : iu);
+}
+
+/* Locate the cell of mesh `mesh` containing the physical point (x, y) and give
+ * the stored index and the point's reference coordinates in that cell. */
+static void locate(const orc_problem* p, int mesh, double x, double y, int* si, int* sj, double* xi,
+                   double* eta) {
+  double hx = hx_of(p), hy = hy_of(p);
+  int iu = (int)floor((x - p->ax) / hx - 0.5 * mesh);
+  double xc = p->ax + (iu + 0.5 + 0.5 * mesh) * hx;
+  *xi = (x - xc) / (0.5 * hx);
+  *si = store_index(p, iu, p->nx);
+  if (p->dim == 2) {
+    int ju = (int)floor((y - p->ay) / hy - 0.5 * mesh);
+    double yc = p->ay + (ju + 0.5 + 0.5 * mesh) * hy;
+    *eta = (y - yc) / (0.5 * hy);
+    *sj = store_index(p, ju, p->ny);
+  } else {
+    *eta = 0.0;
+    *sj = 0;
+  }
+}
+
+/* Basis function (a, b) with derivative orders (dx, dy) in reference
+ * coordinates, converted to physical derivatives. */
+static double basis(const orc_problem* p, int a, int b, int dx, int dy, double xi, double eta) {
+  double v = orc_legendre(a, dx, xi) * pow(2.0 / hx_of(p), dx);
+  if (p->dim == 2) v *= orc_legendre(b, dy, eta) * pow(2.0 / hy_of(p), dy);
+  else if (dy > 0) v = 0.0;
+  return v;
+}
+
+/* Value (dx = dy = 0) or physical derivative of every field of stored cell
+ * (i, j) of mesh `mesh` at reference point (xi, eta). */
+static void cell_eval(const orc_problem* p, const double* u, int mesh, int i, int j, double xi, double eta,
+                      int dx, int dy, double* out) {
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  int M = modes(p, ma, mb), F = nfields(p);
+  for (int f = 0; f < F; ++f) {
+    double s = 0.0;
+    for (int m = 0; m < M; ++m) s += u[sidx(p, mesh, f, m, j, i)] * basis(p, ma[m], mb[m], dx, dy, xi, eta);
+    out[f] = s;
+  }
+}
+
+/* Value of the mesh-`mesh` solution at a physical point. */
+static void point_eval(const orc_problem* p, const double* u, int mesh, double x, double y, double* out) {
+  int si, sj;
+  double xi, eta;
+  locate(p, mesh, x, y, &si, &sj, &xi, &eta);
+  cell_eval(p, u, mesh, si, sj, xi, eta, 0, 0, out);
+}
+
+/* ----------------------------------------------------------------- flux --- */
+
+/* Physical flux components f1(w), f2(w) of the conservation law. Euler:
+ * Section 4, 1D and 2D Euler subsections; advection u_t + a.grad u = 0;
+ * Burgers f = u^2/2 (1D). */
+static void flux(const orc_problem* p, const double* w, double* f1, double* f2) {
+  if (p->system == ORC_ADVECTION) {
+    f1[0] = p->adv_x * w[0];
+    f2[0] = p->adv_y * w[0];
+  } else if (p->system == ORC_BURGERS) {
+    f1[0] = 0.5 * w[0] * w[0];
+    f2[0] = 0.5 * w[0] * w[0];
+  } else if (p->dim == 1) {
+    double rho = w[0], m = w[1], E = w[2];
+    double v = m / rho;
+    double pr = (p->gamma - 1.0) * (E - 0.5 * rho * v * v);
+    f1[0] = m;
+    f1[1] = m * v + pr;
+    f1[2] = (E + pr) * v;
+    f2[0] = f2[1] = f2[2] = 0.0;
+  } else {
+    double rho = w[0], mx = w[1], my = w[2], E = w[3];
+    double vx = mx / rho, vy = my / rho;
+    double pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
+    f1[0] = mx;
+    f1[1] = mx * vx + pr;
+    f1[2] = my * vx;
+    f1[3] = (E + pr) * vx;
+    f2[0] = my;
+    f2[1] = mx * vy;
+    f2[2] = my * vy + pr;
+    f2[3] = (E + pr) * vy;
+  }
+}
+
+/* Spectral radius of n . df/du at state w (the local wave speed beta_{e,K},
+ * Section 2.2 and the Remark on systems).  Returns -1 on a non-physical Euler
+ * state (rho <= 0 or p <= 0). */
+static double wave_speed(const orc_problem* p, const double* w, double nx, double ny) {
+  if (p->system == ORC_ADVECTION) return fabs(p->adv_x * nx + p->adv_y * ny);
+  if (p->system == ORC_BURGERS) return fabs(w[0] * (nx + ny));
+  double rho = w[0];
+  double vx = w[1] / rho, vy = p->dim == 2 ? w[2] / rho : 0.0;
+  double E = w[p->dim + 1];
+  double pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
+  if (!(rho > 0.0) || !(pr > 0.0)) return -1.0;
+  double c = sqrt(p->gamma * pr / rho);
+  return fabs(vx * nx + vy * ny) + c;
+}
+
+/* ------------------------------------------------------- CDG operator H --- */
+
+/* L = M^{-1} R, where R_phi = H(u, phi) restricted to one mesh's test function
+ * phi (Eq. (equcdg)):
+ *   R = (1/tau_max) int_K (w - u_K) phi + int_K f(w) . grad phi
+ *       - sum_e int_e f(w) . n_e phi^-,
+ * with w the overlapping mesh's solution.  Volume integrals: (k+1)^d Gauss
+ * points on each of the 2^d sub-cells of K cut by the overlapping mesh; face
+ * integrals: (k+1) Gauss points on each of the 2 half-faces of every face (1D:
+ * point faces).  Both are exact for a linear flux. */
+static void cell_rhs(const orc_problem* p, const double* u, double inv_tmax, int mesh, int i, int j,
+                     double* L /* [F][M] */) {
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  int M = modes(p, ma, mb), F = nfields(p), k = p->k, nq = k + 1, d = p->dim;
+  int other = 1 - mesh;
+  double hx = hx_of(p), hy = hy_of(p);
+  double gx[ORC_MAXQ], gw[ORC_MAXQ];
+  orc_gauss(nq, gx, gw);
+  double xc, yc;
+  cell_centre(p, mesh, i, j, &xc, &yc);
+  double R[ORC_MAXF][ORC_MAXM];
+  memset(R, 0, sizeof R);
+  double w[ORC_MAXF], uk[ORC_MAXF], f1[ORC_MAXF], f2[ORC_MAXF];
+
+  /* volume and dissipation terms on the sub-cells */
+  int nsy = d == 2 ? 2 : 1, nqy = d == 2 ? nq : 1;
+  for (int sy = 0; sy < nsy; ++sy)
+    for (int sx = 0; sx < 2; ++sx)
+      for (int qy = 0; qy < nqy; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          /* sub-cell s spans [-1+s, s] in reference coordinates */
+          double xi = sx - 0.5 + 0.5 * gx[qx];
+          double eta = d == 2 ? sy - 0.5 + 0.5 * gx[qy] : 0.0;
+          double W = 0.5 * gw[qx] * 0.5 * hx;
+          if (d == 2) W *= 0.5 * gw[qy] * 0.5 * hy;
+          double x = xc + 0.5 * hx * xi, y = yc + 0.5 * hy * eta;
+          point_eval(p, u, other, x, y, w);
+          cell_eval(p, u, mesh, i, j, xi, eta, 0, 0, uk);
+          flux(p, w, f1, f2);
+          for (int m = 0; m < M; ++m) {
+            double ph = basis(p, ma[m], mb[m], 0, 0, xi, eta);
+            double phx = basis(p, ma[m], mb[m], 1, 0, xi, eta);
+            double phy = d == 2 ? basis(p, ma[m], mb[m], 0, 1, xi, eta) : 0.0;
+            for (int f = 0; f < F; ++f)
+              R[f][m] += W * (inv_tmax * (w[f] - uk[f]) * ph + f1[f] * phx + (d == 2 ? f2[f] * phy : 0.0));
+          }
+        }
+
+  /* face terms: - sum_e int_e f(w) . n_e phi^- */
+  for (int face = 0; face < 2 * d; ++face) {
+    int dir = face / 2;            /* 0: x-normal, 1: y-normal */
+    double side = (face % 2) ? 1.0 : -1.0;
+    for (int s = 0; s < (d == 2 ? 2 : 1); ++s)
+      for (int q = 0; q < (d == 2 ? nq : 1); ++q) {
+        double t = d == 2 ? s - 0.5 + 0.5 * gx[q] : 0.0; /* tangential reference coordinate */
+        double xi = dir == 0 ? side : t, eta = dir == 0 ? t : side;
+        double W = d == 2 ? 0.5 * gw[q] * 0.5 * (dir == 0 ? hy : hx) : 1.0;
+        double x = xc + 0.5 * hx * xi, y = yc + 0.5 * hy * eta;
+        point_eval(p, u, other, x, y, w);
+        flux(p, w, f1, f2);
+        for (int m = 0; m < M; ++m) {
+          double ph = basis(p, ma[m], mb[m], 0, 0, xi, d == 2 ? eta : 0.0);
+          for (int f = 0; f < F; ++f) {
+            double fn = dir == 0 ? side * f1[f] : side * f2[f];
+            R[f][m] -= W * fn * ph;
+          }
+        }
+      }
+  }
+
+  /* M^{-1}: the Legendre basis is orthogonal, ||phi_ab||^2 = |K| / ((2a+1)(2b+1)) */
+  for (int m = 0; m < M; ++m) {
+    double nrm = hx / (2.0 * ma[m] + 1.0);
+    if (d == 2) nrm *= hy / (2.0 * mb[m] + 1.0);
+    for (int f = 0; f < F; ++f) L[f * M + m] = R[f][m] / nrm;
+  }
+}
+
+/* Semi-discrete right-hand side dU/dt = L(U) on both meshes. */
+void orc_rhs(const orc_problem* p, const double* u, double tau_max, double* L) {
+  int F = nfields(p), M = nmodes(p);
+  double inv = 1.0 / tau_max;
+  for (int mesh = 0; mesh < 2; ++mesh) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double Lc[ORC_MAXF * ORC_MAXM];
+        cell_rhs(p, u, inv, mesh, i, j, Lc);
+        for (int f = 0; f < F; ++f)
+          for (int m = 0; m < M; ++m) L[sidx(p, mesh, f, m, j, i)] = Lc[f * M + m];
+      }
+  }
+}
+
+/* Bilinear form H(u, phi) for a test function given by its modal coefficients
+ * (both meshes): H(u, phi) = sum_K sum_modes R_K(u) phi_K. */
+double orc_bilinear(const orc_problem* p, const double* u, const double* phi, double tau_max) {
+  int F = nfields(p), M = nmodes(p);
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  modes(p, ma, mb);
+  size_t n = (size_t)2 * F * M * p->ny * p->nx;
+  double* L = (double*)malloc(n * sizeof(double));
+  orc_rhs(p, u, tau_max, L);
+  double hx = hx_of(p), hy = hy_of(p), s = 0.0;
+  for (int mesh = 0; mesh < 2; ++mesh)
+    for (int f = 0; f < F; ++f)
+      for (int m = 0; m < M; ++m) {
+        double nrm = hx / (2.0 * ma[m] + 1.0) * (p->dim == 2 ? hy / (2.0 * mb[m] + 1.0) : 1.0);
+        for (int j = 0; j < p->ny; ++j)
+          for (int i = 0; i < p->nx; ++i) {
+            size_t id = sidx(p, mesh, f, m, j, i);
+            s += nrm * L[id] * phi[id];
+          }
+      }
+  free(L);
+  return s;
+}
+
+/* --------------------------------------------------------- OE procedure --- */
+
+/* Global scales of one mesh, per field (Section 2.2, definition of sigma_K):
+ *   avg(u) = (1/|Omega|) int_Omega u   (cell Gauss rule, stored cells only),
+ *   sigma  = || u - avg(u) ||_{L^inf}, the max taken over the (k+1)^d Gauss
+ *            points of every stored cell (parity unpinned: a convention). */
+static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* avg, double* sig) {
+  int F = nfields(p), nq = p->k + 1, d = p->dim;
+  double gx[ORC_MAXQ], gw[ORC_MAXQ];
+  orc_gauss(nq, gx, gw);
+  double hx = hx_of(p), hy = hy_of(p);
+  int nqy = d == 2 ? nq : 1;
+  double vol = 0.0;
+  double tot[ORC_MAXF] = {0};
+  double v[ORC_MAXF];
+  /* fixed (sequential) summation order */
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i)
+      for (int qy = 0; qy < nqy; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          double W = 0.5 * gw[qx] * hx * (d == 2 ? 0.5 * gw[qy] * hy : 1.0);
+          cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
+          for (int f = 0; f < F; ++f) tot[f] += W * v[f];
+          vol += W;
+        }
+  for (int f = 0; f < F; ++f) {
+    avg[f] = tot[f] / vol;
+    sig[f] = 0.0;
+  }
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i)
+      for (int qy = 0; qy < nqy; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
+          for (int f = 0; f < F; ++f) {
+            double e = fabs(v[f] - avg[f]);
+            if (e > sig[f]) sig[f] = e;
+          }
+        }
+}
+
+static double factorial(int m) {
+  double r = 1.0;
+  for (int i = 2; i <= m; ++i) r *= i;
+  return r;
+}
+
+/* Damping coefficients delta_K^m, m = 0..k, of stored cell (i, j) of mesh
+ * `mesh` (Section 2.2):
+ *   delta_K^m = sum_{e in dK} beta_{e,K} (2m+1) h_{e,K}^{m-1} / ((2k-1) m! sigma_K |e|)
+ *               * int_e ( sum_{|alpha|=m} (d^alpha (u^C - u^D))^2 )^{1/2} ds,
+ * delta = 0 where sigma_K = 0; for systems the max over the components of the
+ * per-component value, for each m (Remark on systems).  u_K is K's own interior
+ * trace on e, the overlapping solution is evaluated at the physical point;
+ * every face is integrated as 2 half-faces with (k+1) Gauss points (1D: the
+ * face is a point and the integral / |e| is the point value).
+ * beta_{e,K} is the normal wave speed at K's cell average.
+ * Returns 0, or ORC_ENONPHYSICAL if the cell average is not a physical state. */
+static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, int j, const double* sig,
+                      double* delta /* [k+1] */) {
+  int F = nfields(p), k = p->k, nq = k + 1, d = p->dim;
+  int other = 1 - mesh;
+  double gx[ORC_MAXQ], gw[ORC_MAXQ];
+  orc_gauss(nq, gx, gw);
+  double hx = hx_of(p), hy = hy_of(p);
+  double xc, yc;
+  cell_centre(p, mesh, i, j, &xc, &yc);
+  double avg[ORC_MAXF];
+  for (int f = 0; f < F; ++f) avg[f] = u[sidx(p, mesh, f, 0, j, i)]; /* mode 0 = cell average */
+  double per_field[ORC_MAXF][ORC_MAXQ];
+  memset(per_field, 0, sizeof per_field);
+  int status = ORC_OK;
+
+  for (int face = 0; face < 2 * d; ++face) {
+    int dir = face / 2;
+    double side = (face % 2) ? 1.0 : -1.0;
+    double nxv = dir == 0 ? side : 0.0, nyv = dir == 1 ? side : 0.0;
+    double beta = wave_speed(p, avg, nxv, nyv);
+    if (beta < 0.0) { status = ORC_ENONPHYSICAL; beta = 0.0; }
+    double he = dir == 0 ? hx : hy;                  /* h_{e,K}: cell width normal to e */
+    double elen = d == 2 ? (dir == 0 ? hy : hx) : 1.0; /* |e| */
+    for (int m = 0; m <= k; ++m) {
+      double integ[ORC_MAXF] = {0};
+      for (int s = 0; s < (d == 2 ? 2 : 1); ++s)
+        for (int q = 0; q < (d == 2 ? nq : 1); ++q) {
+          double t = d == 2 ? s - 0.5 + 0.5 * gx[q] : 0.0;
+          double xi = dir == 0 ? side : t, eta = dir == 0 ? t : side;
+          double W = d == 2 ? 0.5 * gw[q] * 0.5 * elen : 1.0;
+          double x = xc + 0.5 * hx * xi, y = yc + 0.5 * hy * eta;
+          int si, sj;
+          double oxi, oeta;
+          locate(p, other, x, y, &si, &sj, &oxi, &oeta);
+          double sq[ORC_MAXF] = {0};
+          for (int ax = 0; ax <= m; ++ax) {
+            int ay = m - ax;
+            if (d == 1 && ay > 0) continue;
+            double a1[ORC_MAXF], a2[ORC_MAXF];
+            cell_eval(p, u, mesh, i, j, xi, d == 2 ? eta : 0.0, ax, ay, a1);
+            cell_eval(p, u, other, si, sj, oxi, oeta, ax, ay, a2);
+            for (int f = 0; f < F; ++f) {
+              double df = mesh == 0 ? a1[f] - a2[f] : a2[f] - a1[f]; /* u^C - u^D */
+              sq[f] += df * df;
+            }
+          }
+          for (int f = 0; f < F; ++f) integ[f] += W * sqrt(sq[f]);
+        }
+      double coef = beta * (2.0 * m + 1.0) * pow(he, m - 1.0) / ((2.0 * k - 1.0) * factorial(m) * elen);
+      for (int f = 0; f < F; ++f)
+        if (sig[f] != 0.0) per_field[f][m] += coef * integ[f] / sig[f];
+    }
+  }
+  for (int m = 0; m <= k; ++m) {
+    double mx = 0.0;
+    for (int f = 0; f < F; ++f)
+      if (per_field[f][m] > mx) mx = per_field[f][m];
+    delta[m] = mx;
+  }
+  return status;
+}
+
+/* sigma and avg of both meshes (out arrays [2][F]) and delta of every cell
+ * ([2][ny][nx][k+1]).  Returns ORC_ENONPHYSICAL if any cell average is not a
+ * physical state. */
+int orc_oe_coefficients(const orc_problem* p, const double* u, double* delta, double* sigma, double* avg) {
+  int F = nfields(p), K1 = p->k + 1;
+  int status = ORC_OK;
+  for (int mesh = 0; mesh < 2; ++mesh) {
+    double a[ORC_MAXF], s[ORC_MAXF];
+    mesh_sigma(p, u, mesh, a, s);
+    for (int f = 0; f < F; ++f) {
+      if (sigma) sigma[mesh * F + f] = s[f];
+      if (avg) avg[mesh * F + f] = a[f];
+    }
+    int bad = 0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(| : bad)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double dl[ORC_MAXQ];
+        if (cell_delta(p, u, mesh, i, j, s, dl) != ORC_OK) bad = 1;
+        for (int m = 0; m < K1; ++m) delta[(((size_t)mesh * p->ny + j) * p->nx + i) * K1 + m] = dl[m];
+      }
+    if (bad) status = ORC_ENONPHYSICAL;
+  }
+  return status;
+}
+
+/* Exact solution of the damping ODE (OEstep2D) at t_hat = tau.  In the
+ * orthogonal Legendre basis, u - P^{m-1} u keeps exactly the modes of total
+ * degree >= max(m, 1) (P^{-1} := P^0), so mode (a, b) obeys
+ *   d/dt u_ab = -( sum_{m=0}^{min(a+b, k)} delta^m ) u_ab   for a + b >= 1,
+ * and the cell average is untouched. */
+void orc_oe_apply(const orc_problem* p, const double* delta, double tau, double* u) {
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  int M = modes(p, ma, mb), F = nfields(p), K1 = p->k + 1;
+  for (int mesh = 0; mesh < 2; ++mesh)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        const double* dl = delta + (((size_t)mesh * p->ny + j) * p->nx + i) * K1;
+        for (int m = 1; m < M; ++m) {
+          int deg = ma[m] + mb[m];
+          double rate = 0.0;
+          for (int q = 0; q <= p->k && q <= deg; ++q) rate += dl[q];
+          double fac = exp(-tau * rate);
+          for (int f = 0; f < F; ++f) u[sidx(p, mesh, f, m, j, i)] *= fac;
+        }
+      }
+}
+
+/* The OE step F_tau applied in place to both meshes.  k = 0 has no modes to
+ * damp and (2k-1) < 0, so the step is the identity there. */
+int orc_oe(const orc_problem* p, double* u, double tau) {
+  if (p->k == 0) return ORC_OK;
+  size_t nd = (size_t)2 * p->ny * p->nx * (p->k + 1);
+  double* delta = (double*)malloc(nd * sizeof(double));
+  int st = orc_oe_coefficients(p, u, delta, NULL, NULL);
+  orc_oe_apply(p, delta, tau, u);
+  free(delta);
+  return st;
+}
+
+/* ------------------------------------------------------------ time step --- */
+
+/* tau_max from the CFL condition at the start of a step (Section 2.1 and
+ * Section 4): 1D  C_CFL h / beta;  2D  C_CFL / (beta_x/h_x + beta_y/h_y), with
+ * beta the maximum wave speed over the cell averages of both meshes.
+ * Returns ORC_ENONPHYSICAL on a non-physical cell average. */
+int orc_tau_max(const orc_problem* p, const double* u, double* tau_max) {
+  int F = nfields(p);
+  double bxm = 0.0, bym = 0.0;
+  int st = ORC_OK;
+  for (int mesh = 0; mesh < 2; ++mesh)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double w[ORC_MAXF];
+        for (int f = 0; f < F; ++f) w[f] = u[sidx(p, mesh, f, 0, j, i)];
+        double sx = wave_speed(p, w, 1.0, 0.0);
+        double sy = p->dim == 2 ? wave_speed(p, w, 0.0, 1.0) : 0.0;
+        if (sx < 0.0 || sy < 0.0) { st = ORC_ENONPHYSICAL; continue; }
+        if (sx > bxm) bxm = sx;
+        if (sy > bym) bym = sy;
+      }
+  double hx = hx_of(p), hy = hy_of(p);
+  double rate = bxm / hx + (p->dim == 2 ? bym / hy : 0.0);
+  *tau_max = rate > 0.0 ? p->cfl / rate : 0.0;
+  return st;
+}
+
+/* One stage combination of the Shu-Osher form: out = sum_m c_m U_m + tau d L(U_last). */
+static void axpy_stage(size_t n, double* out, const double* a, double ca, const double* b, double cb,
+                       const double* L, double cl) {
+  for (size_t q = 0; q < n; ++q) out[q] = ca * a[q] + cb * b[q] + cl * L[q];
+}
+
+/* One full time step of Eq. (eq:RKCDG) in place: the stages of the chosen RK
+ * method, each followed by the OE step F_tau (if enabled). */
+int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
+  int F = nfields(p), M = nmodes(p);
+  size_t n = (size_t)2 * F * M * p->ny * p->nx;
+  double* L = (double*)malloc(n * sizeof(double));
+  double* u1 = (double*)malloc(n * sizeof(double));
+  double* u2 = (double*)malloc(n * sizeof(double));
+  double* u3 = (double*)malloc(n * sizeof(double));
+  int st = ORC_OK, s;
+#define OE(x)                          \
+  do {                                 \
+    if (p->oe) {                       \
+      s = orc_oe(p, (x), tau);         \
+      if (s != ORC_OK) st = s;         \
+    }                                  \
+  } while (0)
+  if (p->rk == 1) {
+    orc_rhs(p, u, tau_max, L);
+    axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
+    OE(u1);
+    memcpy(u, u1, n * sizeof(double));
+  } else if (p->rk == 2) {
+    orc_rhs(p, u, tau_max, L);
+    axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
+    OE(u1);
+    orc_rhs(p, u1, tau_max, L);
+    axpy_stage(n, u2, u, 0.5, u1, 0.5, L, 0.5 * tau);
+    OE(u2);
+    memcpy(u, u2, n * sizeof(double));
+  } else if (p->rk == 3) {
+    orc_rhs(p, u, tau_max, L);
+    axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
+    OE(u1);
+    orc_rhs(p, u1, tau_max, L);
+    axpy_stage(n, u2, u, 0.75, u1, 0.25, L, 0.25 * tau);
+    OE(u2);
+    orc_rhs(p, u2, tau_max, L);
+    axpy_stage(n, u3, u, 1.0 / 3.0, u2, 2.0 / 3.0, L, 2.0 / 3.0 * tau);
+    OE(u3);
+    memcpy(u, u3, n * sizeof(double));
+  } else {
+    /* classical RK4 in Shu-Osher form */
+    double* u4 = (double*)malloc(n * sizeof(double));
+    orc_rhs(p, u, tau_max, L);
+    axpy_stage(n, u1, u, 1.0, u, 0.0, L, 0.5 * tau);
+    OE(u1);
+    orc_rhs(p, u1, tau_max, L);
+    axpy_stage(n, u2, u, 1.0, u, 0.0, L, 0.5 * tau);
+    OE(u2);
+    orc_rhs(p, u2, tau_max, L);
+    axpy_stage(n, u3, u, 1.0, u, 0.0, L, tau);
+    OE(u3);
+    orc_rhs(p, u3, tau_max, L);
+    for (size_t q = 0; q < n; ++q)
+      u4[q] = -u[q] / 3.0 + u1[q] / 3.0 + 2.0 * u2[q] / 3.0 + u3[q] / 3.0 + tau / 6.0 * L[q];
+    OE(u4);
+    memcpy(u, u4, n * sizeof(double));
+    free(u4);
+  }
+#undef OE
+  free(L);
+  free(u1);
+  free(u2);
+  free(u3);
+  return st;
+}
+
+/* Advance from time *t by up to nsteps steps, stopping at T_end (T_end <= 0: no
+ * end time).  tau_max is recomputed at the start of every step; tau = tau_max,
+ * except that the step that reaches T_end is clipped to T_end - t (and a step
+ * that would leave a sliver shorter than 1e-12 T_end is stretched to T_end).
+ * Returns the status; *t is advanced and *steps_done counts the steps taken. */
+int orc_advance(const orc_problem* p, double* u, double* t, double T_end, int nsteps, int* steps_done) {
+  int st = ORC_OK;
+  int done = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    if (T_end > 0.0 && *t >= T_end) break;
+    double tm;
+    int q = orc_tau_max(p, u, &tm);
+    if (q != ORC_OK) { st = q; break; }
+    double tau = tm;
+    if (T_end > 0.0 && (T_end - (*t + tm) < 1e-12 * T_end)) tau = T_end - *t;
+    q = orc_step_tau(p, u, tau, tm);
+    if (q != ORC_OK) st = q;
+    *t = (T_end > 0.0 && tau == T_end - *t) ? T_end : *t + tau;
+    ++done;
+  }
+  if (steps_done) *steps_done = done;
+  return st;
+}
+
+/* ------------------------------------------------- initial projection --- */
+
+/* Composite Gauss points for sampling the initial data: on every stored cell
+ * of both meshes, (k+1)^d Gauss points on each of its 2^d sub-cells.  Layout:
+ * [mesh][j][i][sy][sx][qy][qx] with (x, y) pairs (1D: x only, layout
+ * [mesh][i][sx][qx]).  Returns the number of points. */
+size_t orc_quad_points(const orc_problem* p, double* xy) {
+  int nq = p->k + 1, d = p->dim;
+  double gx[ORC_MAXQ], gw[ORC_MAXQ];
+  orc_gauss(nq, gx, gw);
+  double hx = hx_of(p), hy = hy_of(p);
+  size_t n = 0;
+  for (int mesh = 0; mesh < 2; ++mesh)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double xc, yc;
+        cell_centre(p, mesh, i, j, &xc, &yc);
+        for (int sy = 0; sy < (d == 2 ? 2 : 1); ++sy)
+          for (int sx = 0; sx < 2; ++sx)
+            for (int qy = 0; qy < (d == 2 ? nq : 1); ++qy)
+              for (int qx = 0; qx < nq; ++qx) {
+                double xi = sx - 0.5 + 0.5 * gx[qx];
+                double eta = sy - 0.5 + 0.5 * gx[qy];
+                if (xy) {
+                  xy[n * d] = xc + 0.5 * hx * xi;
+                  if (d == 2) xy[n * d + 1] = yc + 0.5 * hy * eta;
+                }
+                ++n;
+              }
+      }
+  return n;
+}
+
+/* L^2 projection of sampled initial data onto both meshes (the
+ * projection-based initialisation of Section 3.3), with the composite Gauss rule
+ * of orc_quad_points: u_ab = (int_K u0 phi_ab) / ||phi_ab||^2.
+ * vals layout: [point][F]. */
+void orc_project(const orc_problem* p, const double* vals, double* u) {
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  int M = modes(p, ma, mb), F = nfields(p), nq = p->k + 1, d = p->dim;
+  double gx[ORC_MAXQ], gw[ORC_MAXQ];
+  orc_gauss(nq, gx, gw);
+  int per_cell = (d == 2 ? 4 : 2) * (d == 2 ? nq * nq : nq);
+  for (int mesh = 0; mesh < 2; ++mesh)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        size_t base = (((size_t)mesh * p->ny + j) * p->nx + i) * per_cell;
+        double acc[ORC_MAXF][ORC_MAXM];
+        memset(acc, 0, sizeof acc);
+        size_t n = 0;
+        for (int sy = 0; sy < (d == 2 ? 2 : 1); ++sy)
+          for (int sx = 0; sx < 2; ++sx)
+            for (int qy = 0; qy < (d == 2 ? nq : 1); ++qy)
+              for (int qx = 0; qx < nq; ++qx) {
+                double xi = sx - 0.5 + 0.5 * gx[qx];
+                double eta = sy - 0.5 + 0.5 * gx[qy];
+                /* reference-square weights: the sub-cell has half the width */
+                double W = 0.5 * gw[qx] * (d == 2 ? 0.5 * gw[qy] : 1.0);
+                for (int m = 0; m < M; ++m) {
+                  double ph = orc_legendre(ma[m], 0, xi) * (d == 2 ? orc_legendre(mb[m], 0, eta) : 1.0);
+                  for (int f = 0; f < F; ++f) acc[f][m] += W * vals[(base + n) * F + f] * ph;
+                }
+                ++n;
+              }
+        for (int m = 0; m < M; ++m) {
+          /* ||phi||^2 on the reference cell [-1,1]^d */
+          double nrm = 2.0 / (2.0 * ma[m] + 1.0) * (d == 2 ? 2.0 / (2.0 * mb[m] + 1.0) : 1.0);
+          for (int f = 0; f < F; ++f) u[sidx(p, mesh, f, m, j, i)] = acc[f][m] / nrm;
+        }
+      }
+}
+
+/* ------------------------------------------------------------ utilities --- */
+
+/* Evaluate the solution of mesh `mesh` (field values) at nq reference points
+ * (xi[q], eta[q]) of every stored cell: out[j][i][q][F]. */
+void orc_eval_cells(const orc_problem* p, const double* u, int mesh, int nq, const double* xi,
+                    const double* eta, double* out) {
+  int F = nfields(p);
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i)
+      for (int q = 0; q < nq; ++q)
+        cell_eval(p, u, mesh, i, j, xi[q], p->dim == 2 ? eta[q] : 0.0, 0, 0,
+                  out + ((((size_t)j * p->nx + i) * nq + q) * F));
+}
+
+/* Evaluate the mesh-`mesh` solution at arbitrary physical points (located). */
+void orc_eval_points(const orc_problem* p, const double* u, int mesh, size_t n, const double* xy, double* out) {
+  int F = nfields(p), d = p->dim;
+  for (size_t q = 0; q < n; ++q) point_eval(p, u, mesh, xy[q * d], d == 2 ? xy[q * d + 1] : 0.0, out + q * F);
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

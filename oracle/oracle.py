@@ -1,0 +1,288 @@
+"""ctypes binding of the plain FP64 CPU oracle (oracle/oecdg_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and
+by the CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+The C library is compiled on first use with gcc (``-ffp-contract=off`` so that
+no multiply-add is fused: the oracle rounds every operation separately) into
+``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oecdg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboecdg_oracle.so")
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+BASIS_Q, BASIS_P = 0, 1
+PERIODIC, TRANSMISSIVE = 0, 1
+OK, EINVAL, ENONPHYSICAL = 0, 1, 4
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("k", ctypes.c_int),
+        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int), ("oe", ctypes.c_int),
+        ("rk", ctypes.c_int), ("pad", ctypes.c_int),
+        ("ax", ctypes.c_double), ("bx", ctypes.c_double), ("ay", ctypes.c_double), ("by", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("adv_x", ctypes.c_double), ("adv_y", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library (idempotent).  Returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+               "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib_handle = None
+
+
+def lib():
+    global _lib_handle
+    if _lib_handle is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.POINTER(_Problem)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_legendre.restype = ctypes.c_double
+        L.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.orc_gauss.argtypes = [ctypes.c_int, dp, dp]
+        L.orc_rhs.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_bilinear.restype = ctypes.c_double
+        L.orc_bilinear.argtypes = [P, dp, dp, ctypes.c_double]
+        L.orc_oe_coefficients.restype = ctypes.c_int
+        L.orc_oe_coefficients.argtypes = [P, dp, dp, dp, dp]
+        L.orc_oe_apply.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_oe.restype = ctypes.c_int
+        L.orc_oe.argtypes = [P, dp, ctypes.c_double]
+        L.orc_tau_max.restype = ctypes.c_int
+        L.orc_tau_max.argtypes = [P, dp, dp]
+        L.orc_step_tau.restype = ctypes.c_int
+        L.orc_step_tau.argtypes = [P, dp, ctypes.c_double, ctypes.c_double]
+        L.orc_advance.restype = ctypes.c_int
+        L.orc_advance.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.orc_quad_points.restype = ctypes.c_size_t
+        L.orc_quad_points.argtypes = [P, dp]
+        L.orc_project.argtypes = [P, dp, dp]
+        L.orc_eval_cells.argtypes = [P, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_eval_points.argtypes = [P, dp, ctypes.c_int, ctypes.c_size_t, dp, dp]
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        _lib_handle = L
+    return _lib_handle
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclass
+class Problem:
+    """Oracle problem description (Section 2 / Section 4 of the paper)."""
+    dim: int = 2
+    nx: int = 8
+    ny: int = 8
+    k: int = 2
+    basis: int = BASIS_Q
+    system: int = EULER
+    bc: int = PERIODIC
+    oe: int = 1
+    rk: int = 3
+    ax: float = 0.0
+    bx: float = 1.0
+    ay: float = 0.0
+    by: float = 1.0
+    gamma: float = 1.4
+    adv_x: float = 1.0
+    adv_y: float = 1.0
+    cfl: float = 0.1
+    _c: _Problem = field(default=None, repr=False, compare=False)
+
+    def c(self) -> _Problem:
+        ny = self.ny if self.dim == 2 else 1
+        return _Problem(self.dim, self.nx, ny, self.k, self.basis, self.system, self.bc, self.oe, self.rk, 0,
+                        self.ax, self.bx, self.ay, self.by, self.gamma, self.adv_x, self.adv_y, self.cfl)
+
+    @property
+    def nfields(self) -> int:
+        return self.dim + 2 if self.system == EULER else 1
+
+    @property
+    def nmodes(self) -> int:
+        k = self.k
+        if self.dim == 1:
+            return k + 1
+        return (k + 1) ** 2 if self.basis == BASIS_Q else (k + 1) * (k + 2) // 2
+
+    def modes(self):
+        """(a, b) degree pairs in storage order."""
+        k = self.k
+        if self.dim == 1:
+            return [(a, 0) for a in range(k + 1)]
+        if self.basis == BASIS_Q:
+            return [(a, b) for b in range(k + 1) for a in range(k + 1)]
+        return [(a, s - a) for s in range(k + 1) for a in range(s, -1, -1)]
+
+    @property
+    def shape(self):
+        ny = self.ny if self.dim == 2 else 1
+        return (2, self.nfields, self.nmodes, ny, self.nx)
+
+    @property
+    def hx(self) -> float:
+        return (self.bx - self.ax) / self.nx
+
+    @property
+    def hy(self) -> float:
+        return (self.by - self.ay) / self.ny if self.dim == 2 else 1.0
+
+    def zeros(self) -> np.ndarray:
+        return np.zeros(self.shape, dtype=np.float64)
+
+
+def legendre(n: int, d: int, x: float) -> float:
+    return lib().orc_legendre(n, d, x)
+
+
+def gauss(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss(n, _dp(x), _dp(w))
+    return x, w
+
+
+def rhs(p: Problem, u: np.ndarray, tau_max: float) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    L = np.zeros_like(u)
+    pc = p.c()
+    lib().orc_rhs(ctypes.byref(pc), _dp(u), tau_max, _dp(L))
+    return L
+
+
+def bilinear(p: Problem, u: np.ndarray, phi: np.ndarray, tau_max: float) -> float:
+    """H(u, phi) of Eq. (equcdg) for a test function given by modal coefficients."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    pc = p.c()
+    return lib().orc_bilinear(ctypes.byref(pc), _dp(u), _dp(phi), tau_max)
+
+
+def oe_coefficients(p: Problem, u: np.ndarray):
+    """(delta [2,ny,nx,k+1], sigma [2,F], avg [2,F], status)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    ny = p.ny if p.dim == 2 else 1
+    delta = np.zeros((2, ny, p.nx, p.k + 1))
+    sigma = np.zeros((2, p.nfields))
+    avg = np.zeros((2, p.nfields))
+    pc = p.c()
+    st = lib().orc_oe_coefficients(ctypes.byref(pc), _dp(u), _dp(delta), _dp(sigma), _dp(avg))
+    return delta, sigma, avg, st
+
+
+def oe_apply(p: Problem, u: np.ndarray, delta: np.ndarray, tau: float) -> np.ndarray:
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    pc = p.c()
+    lib().orc_oe_apply(ctypes.byref(pc), _dp(delta), tau, _dp(u))
+    return u
+
+
+def oe(p: Problem, u: np.ndarray, tau: float):
+    """F_tau u (Eq. (OEstep2D) solved exactly).  Returns (u_sigma, status)."""
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    pc = p.c()
+    st = lib().orc_oe(ctypes.byref(pc), _dp(u), tau)
+    return u, st
+
+
+def tau_max(p: Problem, u: np.ndarray):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    pc = p.c()
+    st = lib().orc_tau_max(ctypes.byref(pc), _dp(u), ctypes.byref(out))
+    return out.value, st
+
+
+def step_tau(p: Problem, u: np.ndarray, tau: float, tmax: float):
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    pc = p.c()
+    st = lib().orc_step_tau(ctypes.byref(pc), _dp(u), tau, tmax)
+    return u, st
+
+
+def advance(p: Problem, u: np.ndarray, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1 << 30):
+    """Advance nsteps steps (or to T_end).  Returns (u, t, steps_done, status)."""
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    tt = ctypes.c_double(t)
+    done = ctypes.c_int(0)
+    pc = p.c()
+    st = lib().orc_advance(ctypes.byref(pc), _dp(u), ctypes.byref(tt), T_end, nsteps, ctypes.byref(done))
+    return u, tt.value, done.value, st
+
+
+def quad_points(p: Problem) -> np.ndarray:
+    pc = p.c()
+    n = lib().orc_quad_points(ctypes.byref(pc), None)
+    xy = np.zeros((n, p.dim))
+    lib().orc_quad_points(ctypes.byref(pc), _dp(xy))
+    return xy
+
+
+def project(p: Problem, vals: np.ndarray) -> np.ndarray:
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    u = p.zeros()
+    pc = p.c()
+    lib().orc_project(ctypes.byref(pc), _dp(vals), _dp(u))
+    return u
+
+
+def project_fn(p: Problem, fn) -> np.ndarray:
+    """Project u0 = fn(xy) -> [npts, F] conserved values onto both meshes."""
+    xy = quad_points(p)
+    vals = np.asarray(fn(xy), dtype=np.float64).reshape(len(xy), p.nfields)
+    return project(p, vals)
+
+
+def eval_cells(p: Problem, u: np.ndarray, mesh: int, xi, eta=None) -> np.ndarray:
+    """Field values at reference points of every cell: [ny, nx, nq, F]."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    eta = np.zeros_like(xi) if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    ny = p.ny if p.dim == 2 else 1
+    out = np.zeros((ny, p.nx, len(xi), p.nfields))
+    pc = p.c()
+    lib().orc_eval_cells(ctypes.byref(pc), _dp(u), mesh, len(xi), _dp(xi), _dp(eta), _dp(out))
+    return out
+
+
+def eval_points(p: Problem, u: np.ndarray, mesh: int, xy: np.ndarray) -> np.ndarray:
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, p.dim)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros((len(xy), p.nfields))
+    pc = p.c()
+    lib().orc_eval_points(ctypes.byref(pc), _dp(u), mesh, len(xy), _dp(xy), _dp(out))
+    return out
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(n)
