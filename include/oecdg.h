@@ -1,0 +1,164 @@
+/*
+ * oecdg.h -- C-ABI of the GB300 (sm_103a) FP64 implementation of the
+ * oscillation-eliminating central DG (OECDG) forward time step of
+ * Peng, Wu, Yuan, arXiv:2503.12473.
+ *
+ * Scope of the CUDA path: degree k = 2 only -- the 1D space P^2 (= Q^2 in 1D) and
+ * the 2D tensor space Q^2 -- for linear advection and the compressible Euler
+ * equations, periodic or transmissive boundaries, forward Euler or SSP-RK3.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a cdg_status; nothing throws, aborts or exits.
+ *     cdg_last_error(ctx) returns a static text for the last failure.
+ *   - State arrays are FP64 DEVICE pointers owned by the caller, with
+ *     cdg_state_numel() elements laid out as
+ *         u[mesh][field][mode][j][i]     (i fastest),
+ *     mesh 0 = primal mesh T_h^C, mesh 1 = dual mesh T_h^D (the primal mesh
+ *     shifted by (+hx/2, +hy/2); dual cell (i,j) is centred on primal vertex
+ *     (i+1, j+1)); field = conserved variable (Euler 2D: rho, rho u, rho v, E;
+ *     1D: rho, rho v, E; advection: u); mode = Legendre mode (a,b) of the
+ *     unnormalised Legendre polynomials P_a(xi) P_b(eta) at index b*3 + a in 2D,
+ *     a in 1D.  j is absent (ny = 1) in 1D.
+ *   - All calls are asynchronous on the context's stream unless stated.
+ *   - tau and tau_max live in device memory owned by the context, so that a
+ *     sequence of cdg_step_async calls can be captured in a CUDA graph.
+ *   - Scratch memory (two state-sized buffers, reduction partials) is owned by
+ *     the context and allocated in cdg_init_mesh.
+ */
+#ifndef OECDG_H
+#define OECDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CDG_OK = 0,
+  CDG_EINVAL = 1,        /* invalid argument (null pointer, bad size, bad enum) */
+  CDG_ENOMEM = 2,        /* device allocation failed */
+  CDG_ECUDA = 3,         /* a CUDA runtime call failed */
+  CDG_ENONPHYSICAL = 4,  /* a cell average with rho <= 0 or p <= 0 was met */
+  CDG_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  CDG_EUNSUPPORTED = 6   /* the configuration is outside the CUDA path's scope */
+} cdg_status;
+
+enum { CDG_ADVECTION = 0, CDG_BURGERS = 1, CDG_EULER = 2 };
+enum { CDG_BASIS_Q = 0, CDG_BASIS_P = 1 };
+enum { CDG_PERIODIC = 0, CDG_TRANSMISSIVE = 1 };
+enum { CDG_RK_EULER1 = 1, CDG_RK_SSP3 = 3 };
+
+/* Problem description (Section 2.1 meshes and spaces; Section 4 time stepping). */
+typedef struct {
+  int dim;       /* 1 or 2 */
+  int nx, ny;    /* primal cells per direction (ny is ignored when dim = 1) */
+  int k;         /* polynomial degree; the CUDA path supports k = 2 */
+  int basis;     /* CDG_BASIS_Q (1D: P^2 = Q^2) */
+  int system;    /* CDG_ADVECTION or CDG_EULER */
+  int bc;        /* CDG_PERIODIC or CDG_TRANSMISSIVE on every side */
+  int oe;        /* 1: apply the OE step F_tau after every RK stage */
+  int rk;        /* CDG_RK_EULER1 or CDG_RK_SSP3 */
+  int pad;
+  double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
+  double gamma;          /* ratio of specific heats (Euler) */
+  double adv_x, adv_y;   /* advection velocity */
+  double cfl;            /* C_CFL of the time step, Section 4 */
+} cdg_mesh_desc;
+
+typedef struct cdg_ctx cdg_ctx;
+
+/* Create a context for the mesh pair of Section 2.1 (primal + dual), bound to
+ * `stream` (a cudaStream_t; NULL = the legacy default stream), on the current
+ * device.  Allocates the geometry constants and the scratch buffers.
+ * Errors: CDG_EINVAL (null pointers, sizes < 2, bad enums), CDG_EUNSUPPORTED
+ * (k != 2, basis P in 2D, Burgers), CDG_ENOMEM, CDG_ECUDA.  On error *out is
+ * NULL. */
+cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out);
+
+/* Release a context (synchronises its stream first).  NULL is accepted. */
+cdg_status cdg_free(cdg_ctx* ctx);
+
+/* Static text describing the last error of `ctx` ("" if none; NULL ctx ok). */
+const char* cdg_last_error(const cdg_ctx* ctx);
+
+/* Number of FP64 elements of a state array (2 meshes x fields x modes x cells). */
+cdg_status cdg_state_numel(const cdg_ctx* ctx, size_t* numel);
+
+/* Sampling points of the projection-based initialisation (Section 3.3): on
+ * every cell of both meshes, 3 x 3 (1D: 3) Gauss points on each of its 4
+ * (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx] of (x, y) pairs (1D:
+ * [mesh][i][sx][qx] of x).  With d_xy == NULL only *npts is set; otherwise
+ * d_xy is a device array of npts * dim doubles. */
+cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts);
+
+/* L^2 projection of sampled initial data onto both meshes (the projection-
+ * based initialisation of Section 3.3) with the composite Gauss rule of
+ * cdg_quad_points.  d_vals: device [npts][fields] conserved values at the
+ * points; d_u: device state (output). */
+cdg_status cdg_project_ic(cdg_ctx* ctx, const double* d_vals, double* d_u);
+
+/* Semi-discrete right-hand side of the CDG method, Eq. (equcdg) (1D Eq.
+ * (eq:1D_H), 2D Eq. (eq:2D_H)): d_L = M^{-1} H(u, .) on both meshes, with the
+ * dissipation coefficient 1/tau_max.  d_L must not alias d_u. */
+cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L);
+
+/* Time step of Section 4 (2D: tau_max = C_CFL / (beta_x/h_x + beta_y/h_y);
+ * 1D: C_CFL h / beta) from the maximum wave speed over the cell averages of
+ * both meshes; tau = tau_max, clipped so that t + tau does not pass T_end
+ * (T_end <= 0: no end time).  Stores (tau, tau_max) in the context's device
+ * memory.  A non-physical cell average sets the context's status flag. */
+cdg_status cdg_compute_dt(cdg_ctx* ctx, const double* d_u, double t, double T_end);
+
+/* Set (tau, tau_max) directly (host values). */
+cdg_status cdg_set_dt(cdg_ctx* ctx, double tau, double tau_max);
+
+/* Read (tau, tau_max) back to the host; synchronises the stream. */
+cdg_status cdg_get_dt(cdg_ctx* ctx, double* tau, double* tau_max);
+
+/* One RK stage of Eq. (eq:RKCDG) without the OE step, with the context's tau
+ * and tau_max: SSP-RK3 stage l in {0,1,2}
+ *     d_out = c_l d_un + (1 - c_l) (d_ul + tau L(d_ul)),  c = (0, 3/4, 1/3),
+ * (forward Euler: l = 0 only).  d_out must not alias d_ul or d_un, except that
+ * d_un is not read when l = 0. */
+cdg_status cdg_rk_stage(cdg_ctx* ctx, int l, const double* d_un, const double* d_ul, double* d_out);
+
+/* The OE step u_sigma = F_tau u_h (Eq. (OEstep2D), solved exactly): sigma_K
+ * and avg per mesh and field, the damping coefficients delta_K^m (m = 0..2)
+ * from the traces of u^C - u^D on the half-faces of every cell, the wave speed
+ * beta_{e,K} at the cell average, and the exponential decay of every mode of
+ * total degree >= 1.  tau from the context.  d_usig must not alias d_uh.
+ * A non-physical cell average sets the context's status flag. */
+cdg_status cdg_oe_damp(cdg_ctx* ctx, const double* d_uh, double* d_usig);
+
+/* The damping coefficients alone, for inspection: d_delta [2][ny][nx][3],
+ * d_sigma [2][fields] (either may be NULL). */
+cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta, double* d_sigma);
+
+/* nsteps full time steps of Eq. (eq:RKCDG) in place on d_u, starting at time t
+ * (tau recomputed at the start of every step, clipped at T_end > 0; steps
+ * after T_end is reached are skipped on the device with tau = 0).  Uses the
+ * context's scratch.  Synchronises at the end and returns CDG_ENONPHYSICAL if
+ * the status flag was set. */
+cdg_status cdg_step(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
+
+/* As cdg_step, but without the final synchronisation and status check, so
+ * that it can be captured in a CUDA graph; the time advanced so far is kept on
+ * the device (cdg_get_time). */
+cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
+
+/* Device time after the last cdg_step / cdg_step_async; synchronises. */
+cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
+
+/* Read and clear the device status flag (synchronises): CDG_OK or
+ * CDG_ENONPHYSICAL. */
+cdg_status cdg_check_status(cdg_ctx* ctx);
+
+/* Number of kernels launched by the context so far (host-side counter). */
+cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OECDG_H */

@@ -1,0 +1,342 @@
+// oecdg_api.cu -- the C-ABI of include/oecdg.h: context, argument checks and
+// the stage pipeline of Eq. (eq:RKCDG):
+//   per step:  wave-speed reduction -> (tau, tau_max) on the device
+//   per stage: k_stage (CDG RHS + RK combine + sigma partials) -> k_sigma ->
+//              k_oe (damping coefficients + exact OE step)
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/oecdg.h"
+#include "oecdg_common.cuh"
+#include "oecdg_kernels.h"
+
+using namespace oecdg;
+
+struct cdg_ctx {
+  cdg_mesh_desc d;
+  Geo g;
+  cudaStream_t stream;
+  int F, M;
+  size_t numel;
+  long long nblk;        // stage-kernel blocks per mesh (sigma partials)
+  int wave_blk;          // blocks of the wave-speed reduction
+  double* buf_a;         // scratch state (u_h)
+  double* buf_b;         // scratch state (u_sigma)
+  double* partials;      // [2][nblk][F][3]
+  double* wave_partial;  // [wave_blk][2]
+  double* dt;            // [tau, tau_max]
+  double* rhs_dt;        // [0, tau_max] for cdg_rhs
+  double* time;          // [t, unused]
+  double* sigma;         // [2][F]
+  double* avg;           // [2][F]
+  int* status;           // status bits
+  long long launches;
+  char err[256];
+};
+
+static cdg_status fail(cdg_ctx* c, cdg_status s, const char* msg) {
+  if (c) snprintf(c->err, sizeof c->err, "%s", msg);
+  return s;
+}
+
+static cdg_status cuda_fail(cdg_ctx* c, cudaError_t e, const char* where) {
+  if (c) snprintf(c->err, sizeof c->err, "%s: %s", where, cudaGetErrorString(e));
+  return CDG_ECUDA;
+}
+
+#define CK(expr, where)                          \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+extern "C" {
+
+cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out) {
+  if (out) *out = nullptr;
+  if (!desc || !out) return CDG_EINVAL;
+  const cdg_mesh_desc& d = *desc;
+  if (d.dim != 1 && d.dim != 2) return CDG_EINVAL;
+  if (d.nx < 2 || (d.dim == 2 && d.ny < 2)) return CDG_EINVAL;
+  if (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE) return CDG_EINVAL;
+  if (d.system != CDG_ADVECTION && d.system != CDG_BURGERS && d.system != CDG_EULER) return CDG_EINVAL;
+  if (d.rk != CDG_RK_EULER1 && d.rk != CDG_RK_SSP3) return CDG_EUNSUPPORTED;
+  if (d.k != 2 || d.system == CDG_BURGERS || (d.dim == 2 && d.basis != CDG_BASIS_Q)) return CDG_EUNSUPPORTED;
+  if (!(d.bx > d.ax) || (d.dim == 2 && !(d.by > d.ay)) || !(d.cfl > 0.0)) return CDG_EINVAL;
+  if (d.system == CDG_EULER && !(d.gamma > 1.0)) return CDG_EINVAL;
+  const long long ny = d.dim == 2 ? d.ny : 1;
+  if ((long long)d.nx * ny > (1LL << 31)) return CDG_EINVAL;
+
+  cdg_ctx* c = (cdg_ctx*)calloc(1, sizeof(cdg_ctx));
+  if (!c) return CDG_ENOMEM;
+  c->d = d;
+  c->d.ny = (int)ny;
+  c->stream = (cudaStream_t)stream;
+  c->F = d.system == CDG_EULER ? d.dim + 2 : 1;
+  c->M = d.dim == 2 ? 9 : 3;
+  Geo& g = c->g;
+  g.nx = d.nx;
+  g.ny = (int)ny;
+  g.plane = (long long)d.nx * ny;
+  g.hx = (d.bx - d.ax) / d.nx;
+  g.hy = d.dim == 2 ? (d.by - d.ay) / d.ny : 1.0;
+  g.gamma = d.gamma;
+  g.adv_x = d.adv_x;
+  g.adv_y = d.adv_y;
+  g.cfl = d.cfl;
+  c->numel = (size_t)2 * c->F * c->M * g.plane;
+  c->nblk = d.dim == 2 ? partial_blocks_2d(g) : partial_blocks_1d(g);
+  c->wave_blk = d.dim == 2 ? wave_blocks_2d(g) : wave_blocks_1d(g);
+
+  cudaError_t e = cudaSuccess;
+  void* p = nullptr;
+#define ALLOC(field, bytes)                         \
+  do {                                              \
+    e = cudaMalloc(&p, (bytes));                    \
+    if (e != cudaSuccess) goto nomem;               \
+    c->field = (decltype(c->field))p;               \
+  } while (0)
+  ALLOC(buf_a, c->numel * sizeof(double));
+  ALLOC(buf_b, c->numel * sizeof(double));
+  ALLOC(partials, (size_t)2 * c->nblk * c->F * 3 * sizeof(double));
+  ALLOC(wave_partial, (size_t)c->wave_blk * 2 * sizeof(double));
+  ALLOC(dt, 2 * sizeof(double));
+  ALLOC(rhs_dt, 2 * sizeof(double));
+  ALLOC(time, 2 * sizeof(double));
+  ALLOC(sigma, (size_t)2 * c->F * sizeof(double));
+  ALLOC(avg, (size_t)2 * c->F * sizeof(double));
+  ALLOC(status, sizeof(int));
+#undef ALLOC
+  e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, 2 * sizeof(double), c->stream);
+  if (e != cudaSuccess) {
+    cdg_free(c);
+    return CDG_ECUDA;
+  }
+  *out = c;
+  return CDG_OK;
+nomem:
+  cdg_free(c);
+  return CDG_ENOMEM;
+}
+
+cdg_status cdg_free(cdg_ctx* c) {
+  if (!c) return CDG_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->buf_a);
+  cudaFree(c->buf_b);
+  cudaFree(c->partials);
+  cudaFree(c->wave_partial);
+  cudaFree(c->dt);
+  cudaFree(c->rhs_dt);
+  cudaFree(c->time);
+  cudaFree(c->sigma);
+  cudaFree(c->avg);
+  cudaFree(c->status);
+  free(c);
+  return CDG_OK;
+}
+
+const char* cdg_last_error(const cdg_ctx* c) { return c ? c->err : ""; }
+
+cdg_status cdg_state_numel(const cdg_ctx* c, size_t* n) {
+  if (!c || !n) return CDG_EINVAL;
+  *n = c->numel;
+  return CDG_OK;
+}
+
+cdg_status cdg_launch_count(const cdg_ctx* c, long long* n) {
+  if (!c || !n) return CDG_EINVAL;
+  *n = c->launches;
+  return CDG_OK;
+}
+
+cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts) {
+  if (!ctx || !npts) return CDG_EINVAL;
+  const size_t per = ctx->d.dim == 2 ? 36 : 6;
+  *npts = (size_t)2 * ctx->g.plane * per;
+  if (!d_xy) return CDG_OK;
+  if (ctx->d.dim == 2) CK(launch_points2d(ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
+  else CK(launch_points1d(ctx->g, ctx->d.ax, d_xy, ctx->stream), "quad_points");
+  ctx->launches += 1;
+  return CDG_OK;
+}
+
+cdg_status cdg_project_ic(cdg_ctx* ctx, const double* d_vals, double* d_u) {
+  if (!ctx || !d_vals || !d_u) return fail(ctx, CDG_EINVAL, "project_ic: null pointer");
+  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
+  if (ctx->d.dim == 2) CK(launch_project2d(sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  else CK(launch_project1d(sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  ctx->launches += 1;
+  return CDG_OK;
+}
+
+static cudaError_t run_stage(cdg_ctx* ctx, int rhs_only, const double* uin, const double* un, double* out,
+                             const double* dt, double ca, double cb) {
+  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
+  const int bc = ctx->d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
+  ctx->launches += 1;
+  if (ctx->d.dim == 2)
+    return launch_stage2d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+  return launch_stage1d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+}
+
+// sigma from the partials of the last stage kernel, then the OE kernel
+static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* delta) {
+  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
+  const int bc = ctx->d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
+  cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream);
+  if (e != cudaSuccess) return e;
+  ctx->launches += 2;
+  if (ctx->d.dim == 2)
+    return launch_oe2d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+  return launch_oe1d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+}
+
+cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L) {
+  if (!ctx || !d_u || !d_L) return fail(ctx, CDG_EINVAL, "rhs: null pointer");
+  if (d_u == d_L) return fail(ctx, CDG_EINVAL, "rhs: d_L aliases d_u");
+  if (!(tau_max > 0.0)) return fail(ctx, CDG_EINVAL, "rhs: tau_max must be > 0");
+  CK(launch_set2(ctx->rhs_dt, 0.0, tau_max, ctx->stream), "rhs");
+  ctx->launches += 1;
+  CK(run_stage(ctx, 1, d_u, nullptr, d_L, ctx->rhs_dt, 0.0, 1.0), "rhs");
+  return CDG_OK;
+}
+
+static cudaError_t launch_dt(cdg_ctx* ctx, const double* d_u, double T_end) {
+  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
+  ctx->launches += 2;
+  if (ctx->d.dim == 2)
+    return launch_dt2d(sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
+                       ctx->stream);
+  return launch_dt1d(sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
+                     ctx->stream);
+}
+
+cdg_status cdg_compute_dt(cdg_ctx* ctx, const double* d_u, double t, double T_end) {
+  if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "compute_dt: null pointer");
+  CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "compute_dt");
+  ctx->launches += 1;
+  CK(launch_dt(ctx, d_u, T_end), "compute_dt");
+  return CDG_OK;
+}
+
+cdg_status cdg_set_dt(cdg_ctx* ctx, double tau, double tau_max) {
+  if (!ctx) return CDG_EINVAL;
+  if (!(tau >= 0.0) || !(tau_max > 0.0)) return fail(ctx, CDG_EINVAL, "set_dt: need tau >= 0, tau_max > 0");
+  CK(launch_set2(ctx->dt, tau, tau_max, ctx->stream), "set_dt");
+  ctx->launches += 1;
+  return CDG_OK;
+}
+
+cdg_status cdg_get_dt(cdg_ctx* ctx, double* tau, double* tau_max) {
+  if (!ctx || !tau || !tau_max) return CDG_EINVAL;
+  double h[2];
+  CK(cudaMemcpyAsync(h, ctx->dt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "get_dt");
+  CK(cudaStreamSynchronize(ctx->stream), "get_dt");
+  *tau = h[0];
+  *tau_max = h[1];
+  return CDG_OK;
+}
+
+cdg_status cdg_get_time(cdg_ctx* ctx, double* t) {
+  if (!ctx || !t) return CDG_EINVAL;
+  CK(cudaMemcpyAsync(t, ctx->time, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "get_time");
+  CK(cudaStreamSynchronize(ctx->stream), "get_time");
+  return CDG_OK;
+}
+
+// SSP-RK3 (Shu-Osher) stage coefficients: out = c_l un + (1 - c_l)(ul + tau L(ul))
+static const double SSP3_C[3] = {0.0, 0.75, 1.0 / 3.0};
+
+cdg_status cdg_rk_stage(cdg_ctx* ctx, int l, const double* d_un, const double* d_ul, double* d_out) {
+  if (!ctx || !d_ul || !d_out) return fail(ctx, CDG_EINVAL, "rk_stage: null pointer");
+  const int nst = ctx->d.rk == CDG_RK_SSP3 ? 3 : 1;
+  if (l < 0 || l >= nst) return fail(ctx, CDG_EINVAL, "rk_stage: stage index out of range");
+  if (l > 0 && !d_un) return fail(ctx, CDG_EINVAL, "rk_stage: d_un is null");
+  if (d_out == d_ul || (l > 0 && d_out == d_un)) return fail(ctx, CDG_EINVAL, "rk_stage: output aliases an input");
+  const double ca = nst == 3 ? SSP3_C[l] : 0.0;
+  CK(run_stage(ctx, 0, d_ul, d_un, d_out, ctx->dt, ca, 1.0 - ca), "rk_stage");
+  return CDG_OK;
+}
+
+cdg_status cdg_oe_damp(cdg_ctx* ctx, const double* d_uh, double* d_usig) {
+  if (!ctx || !d_uh || !d_usig) return fail(ctx, CDG_EINVAL, "oe_damp: null pointer");
+  if (d_uh == d_usig) return fail(ctx, CDG_EINVAL, "oe_damp: d_usig aliases d_uh");
+  // sigma partials of d_uh: a stage with tau = 0 copies d_uh into scratch and
+  // leaves the partials of d_uh behind (this standalone entry point is not on
+  // the cdg_step path, where the partials come from the stage that made u_h)
+  CK(launch_set2(ctx->rhs_dt, 0.0, 1.0, ctx->stream), "oe_damp");
+  ctx->launches += 1;
+  CK(run_stage(ctx, 0, d_uh, nullptr, ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt, 0.0, 1.0),
+     "oe_damp");
+  if (ctx->d.k == 0) return CDG_OK;
+  CK(run_oe(ctx, d_uh, d_usig, nullptr), "oe_damp");
+  return CDG_OK;
+}
+
+cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta, double* d_sigma) {
+  if (!ctx || !d_uh) return fail(ctx, CDG_EINVAL, "oe_coefficients: null pointer");
+  CK(launch_set2(ctx->rhs_dt, 0.0, 1.0, ctx->stream), "oe_coefficients");
+  ctx->launches += 1;
+  CK(run_stage(ctx, 0, d_uh, nullptr, ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt, 0.0, 1.0),
+     "oe_coefficients");
+  if (d_delta) CK(run_oe(ctx, d_uh, nullptr, d_delta), "oe_coefficients");
+  else {
+    CK(launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream),
+       "oe_coefficients");
+    ctx->launches += 1;
+  }
+  if (d_sigma)
+    CK(cudaMemcpyAsync(d_sigma, ctx->sigma, (size_t)2 * ctx->F * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->stream),
+       "oe_coefficients");
+  return CDG_OK;
+}
+
+cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
+  if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "step: null pointer");
+  if (nsteps < 0) return fail(ctx, CDG_EINVAL, "step: nsteps < 0");
+  if (d_u == ctx->buf_a || d_u == ctx->buf_b) return fail(ctx, CDG_EINVAL, "step: d_u is a context buffer");
+  CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step");
+  ctx->launches += 1;
+  const int nst = ctx->d.rk == CDG_RK_SSP3 ? 3 : 1;
+  for (int s = 0; s < nsteps; ++s) {
+    CK(launch_dt(ctx, d_u, T_end), "step: dt");
+    // u_h^{(l+1)} -> buf_a, u_sigma^{(l+1)} -> buf_b (last stage: back into d_u)
+    for (int l = 0; l < nst; ++l) {
+      const double ca = nst == 3 ? SSP3_C[l] : 0.0;
+      const double* uin = l == 0 ? d_u : ctx->buf_b;
+      CK(run_stage(ctx, 0, uin, d_u, ctx->buf_a, ctx->dt, ca, 1.0 - ca), "step: stage");
+      double* dst = (l == nst - 1) ? d_u : ctx->buf_b;
+      if (ctx->d.oe) {
+        CK(run_oe(ctx, ctx->buf_a, dst, nullptr), "step: oe");
+      } else {
+        CK(cudaMemcpyAsync(dst, ctx->buf_a, ctx->numel * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+           "step: copy");
+      }
+    }
+  }
+  return CDG_OK;
+}
+
+cdg_status cdg_check_status(cdg_ctx* ctx) {
+  if (!ctx) return CDG_EINVAL;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "check_status");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "check_status");
+  CK(cudaStreamSynchronize(ctx->stream), "check_status");
+  if (h & ST_NONPHYSICAL) return fail(ctx, CDG_ENONPHYSICAL, "non-physical cell average (rho <= 0 or p <= 0)");
+  return CDG_OK;
+}
+
+cdg_status cdg_step(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
+  cdg_status s = cdg_step_async(ctx, d_u, t, T_end, nsteps);
+  if (s != CDG_OK) return s;
+  return cdg_check_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// oecdg_common.cuh -- device constants and helpers of the OECDG CUDA path
+// (arXiv:2503.12473).  Degree k = 2: 3-point Gauss-Legendre rule, unnormalised
+// Legendre polynomials P_0 = 1, P_1 = x, P_2 = (3x^2 - 1)/2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace oecdg {
+
+enum { SYS_ADV = 0, SYS_BURGERS = 1, SYS_EULER = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+
+// status bits written by kernels
+enum { ST_NONPHYSICAL = 1 };
+
+// 3-point Gauss-Legendre rule on [-1, 1]: nodes -sqrt(3/5), 0, sqrt(3/5),
+// weights 5/9, 8/9, 5/9.
+constexpr double GQ = 0.77459666924148337704;  // sqrt(3/5)
+
+__host__ __device__ constexpr double gnode(int q) { return q == 0 ? -GQ : (q == 1 ? 0.0 : GQ); }
+__host__ __device__ constexpr double gwt(int q) { return q == 1 ? (8.0 / 9.0) : (5.0 / 9.0); }
+
+// Legendre P_n and derivatives (n <= 2)
+__host__ __device__ constexpr double lp(int n, double x) { return n == 0 ? 1.0 : (n == 1 ? x : 1.5 * x * x - 0.5); }
+__host__ __device__ constexpr double dlp(int n, double x) { return n == 0 ? 0.0 : (n == 1 ? 1.0 : 3.0 * x); }
+__host__ __device__ constexpr double ddlp(int n) { return n == 2 ? 3.0 : 0.0; }
+
+// Points of sub-cell s (s = 0: [-1, 0], s = 1: [0, 1]) in the cell's own
+// reference coordinate, and the same physical points in the overlapping cell of
+// the other mesh (its centre sits on this cell's face: xi' = xi + 1 - 2s).
+__host__ __device__ constexpr double xs_self(int s, int q) { return s - 0.5 + 0.5 * gnode(q); }
+__host__ __device__ constexpr double xs_other(int s, int q) { return 0.5 - s + 0.5 * gnode(q); }
+
+template <int BC>
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  if (BC == BC_PERIODIC) return i < 0 ? i + n : (i >= n ? i - n : i);
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Geometry and physics constants passed by value to every kernel.
+struct Geo {
+  int nx, ny;
+  long long plane;   // nx * ny (cells of one mesh)
+  double hx, hy;
+  double gamma;
+  double adv_x, adv_y;
+  double cfl;
+};
+
+// 2D Euler flux components at a conserved state (rho, mx, my, E).
+struct Euler2 {
+  __device__ static __forceinline__ void both(const double* w, double g, double* f1, double* f2) {
+    const double r = __drcp_rn(w[0]);
+    const double vx = w[1] * r, vy = w[2] * r;
+    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    const double H = w[3] + p;
+    f1[0] = w[1];
+    f1[1] = fma(w[1], vx, p);
+    f1[2] = w[2] * vx;
+    f1[3] = H * vx;
+    f2[0] = w[2];
+    f2[1] = f1[2];
+    f2[2] = fma(w[2], vy, p);
+    f2[3] = H * vy;
+  }
+  __device__ static __forceinline__ void fx(const double* w, double g, double* f1) {
+    const double r = __drcp_rn(w[0]);
+    const double vx = w[1] * r, vy = w[2] * r;
+    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    f1[0] = w[1];
+    f1[1] = fma(w[1], vx, p);
+    f1[2] = w[2] * vx;
+    f1[3] = (w[3] + p) * vx;
+  }
+  __device__ static __forceinline__ void fy(const double* w, double g, double* f2) {
+    const double r = __drcp_rn(w[0]);
+    const double vx = w[1] * r, vy = w[2] * r;
+    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    f2[0] = w[2];
+    f2[1] = w[1] * vy;
+    f2[2] = fma(w[2], vy, p);
+    f2[3] = (w[3] + p) * vy;
+  }
+};
+
+// Block-level reductions (sum, max, min) over blockDim.x threads (a multiple
+// of 32, at most 1024).  `sh` holds 3 * 32 doubles.  Result valid in thread 0.
+__device__ __forceinline__ void block_reduce3(double& s, double& mx, double& mn, double* sh) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(full, s, o);
+    mx = fmax(mx, __shfl_down_sync(full, mx, o));
+    mn = fmin(mn, __shfl_down_sync(full, mn, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[warp] = s;
+    sh[32 + warp] = mx;
+    sh[64 + warp] = mn;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < nw ? sh[lane] : 0.0;
+    mx = lane < nw ? sh[32 + lane] : -1.0 / 0.0;
+    mn = lane < nw ? sh[64 + lane] : 1.0 / 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(full, s, o);
+      mx = fmax(mx, __shfl_down_sync(full, mx, o));
+      mn = fmin(mn, __shfl_down_sync(full, mn, o));
+    }
+  }
+}
+
+__device__ __forceinline__ double block_reduce_max(double v, double* sh) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(full, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(full, v, o));
+  }
+  return v;
+}
+
+}  // namespace oecdg

@@ -1,0 +1,39 @@
+// oecdg_kernels.h -- internal launch functions of the OECDG CUDA path.
+#pragma once
+#include <cuda_runtime.h>
+#include "oecdg_common.cuh"
+
+namespace oecdg {
+
+// 2D Q^2
+long long partial_blocks_2d(const Geo& g);
+int wave_blocks_2d(const Geo& g);
+cudaError_t launch_stage2d(int sys, int bc, const Geo& g, int rhs_only, const double* uin, const double* un,
+                           double* out, const double* dt, double ca, double cb, double* partials, cudaStream_t st);
+cudaError_t launch_oe2d(int sys, int bc, const Geo& g, const double* uh, double* usig, const double* dt,
+                        const double* sigma, double* delta, int* status, cudaStream_t st);
+cudaError_t launch_dt2d(int sys, const Geo& g, const double* u, double* partial, int nblk, double T_end, double* dt,
+                        double* time, int* status, cudaStream_t st);
+cudaError_t launch_points2d(const Geo& g, double ax, double ay, double* xy, cudaStream_t st);
+cudaError_t launch_project2d(int sys, const Geo& g, const double* vals, double* u, cudaStream_t st);
+
+// 1D P^2
+long long partial_blocks_1d(const Geo& g);
+int wave_blocks_1d(const Geo& g);
+cudaError_t launch_stage1d(int sys, int bc, const Geo& g, int rhs_only, const double* uin, const double* un,
+                           double* out, const double* dt, double ca, double cb, double* partials, cudaStream_t st);
+cudaError_t launch_oe1d(int sys, int bc, const Geo& g, const double* uh, double* usig, const double* dt,
+                        const double* sigma, double* delta, int* status, cudaStream_t st);
+cudaError_t launch_dt1d(int sys, const Geo& g, const double* u, double* partial, int nblk, double T_end, double* dt,
+                        double* time, int* status, cudaStream_t st);
+cudaError_t launch_points1d(const Geo& g, double ax, double* x, cudaStream_t st);
+cudaError_t launch_project1d(int sys, const Geo& g, const double* vals, double* u, cudaStream_t st);
+
+// shared
+cudaError_t launch_sigma(const double* partials, long long nblk, int F, long long ncell, double* sigma, double* avg,
+                         cudaStream_t st);
+cudaError_t launch_set2(double* p, double a, double b, cudaStream_t st);
+cudaError_t launch_dt_final(const double* partial, int nblk, double hx, double hy, int dim, double cfl, double T_end,
+                            double* dt, double* time, cudaStream_t st);
+
+}  // namespace oecdg

@@ -1,0 +1,277 @@
+"""Thin Python binding of the OECDG C-ABI (include/oecdg.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library
+``paper_2503_12473_gb300/_build/liboecdg.so``.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+Device memory and streams come from PyTorch: state arrays are contiguous
+float64 CUDA tensors, passed by ``data_ptr()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+CDG_OK, CDG_EINVAL, CDG_ENOMEM, CDG_ECUDA, CDG_ENONPHYSICAL, CDG_ETIMEOUT, CDG_EUNSUPPORTED = range(7)
+ADVECTION, BURGERS, EULER = 0, 1, 2
+BASIS_Q, BASIS_P = 0, 1
+PERIODIC, TRANSMISSIVE = 0, 1
+RK_EULER1, RK_SSP3 = 1, 3
+
+STATUS_NAMES = {0: "CDG_OK", 1: "CDG_EINVAL", 2: "CDG_ENOMEM", 3: "CDG_ECUDA", 4: "CDG_ENONPHYSICAL",
+                5: "CDG_ETIMEOUT", 6: "CDG_EUNSUPPORTED"}
+
+EXPORTED = [
+    "cdg_init_mesh", "cdg_free", "cdg_last_error", "cdg_state_numel", "cdg_quad_points", "cdg_project_ic",
+    "cdg_rhs", "cdg_compute_dt", "cdg_set_dt", "cdg_get_dt", "cdg_rk_stage", "cdg_oe_damp",
+    "cdg_oe_coefficients", "cdg_step", "cdg_step_async", "cdg_get_time", "cdg_check_status", "cdg_launch_count",
+]
+
+
+class CdgError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cdg_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("k", ctypes.c_int),
+        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int), ("oe", ctypes.c_int),
+        ("rk", ctypes.c_int), ("pad", ctypes.c_int),
+        ("ax", ctypes.c_double), ("bx", ctypes.c_double), ("ay", ctypes.c_double), ("by", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("adv_x", ctypes.c_double), ("adv_y", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"OECDG CUDA library missing: {path}")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    st = ctypes.c_int
+    L.cdg_init_mesh.restype = st
+    L.cdg_init_mesh.argtypes = [ctypes.POINTER(cdg_mesh_desc), vp, ctypes.POINTER(vp)]
+    L.cdg_free.restype = st
+    L.cdg_free.argtypes = [vp]
+    L.cdg_last_error.restype = ctypes.c_char_p
+    L.cdg_last_error.argtypes = [vp]
+    L.cdg_state_numel.restype = st
+    L.cdg_state_numel.argtypes = [vp, ctypes.POINTER(sz)]
+    L.cdg_quad_points.restype = st
+    L.cdg_quad_points.argtypes = [vp, vp, ctypes.POINTER(sz)]
+    L.cdg_project_ic.restype = st
+    L.cdg_project_ic.argtypes = [vp, vp, vp]
+    L.cdg_rhs.restype = st
+    L.cdg_rhs.argtypes = [vp, vp, ctypes.c_double, vp]
+    L.cdg_compute_dt.restype = st
+    L.cdg_compute_dt.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
+    L.cdg_set_dt.restype = st
+    L.cdg_set_dt.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.cdg_get_dt.restype = st
+    L.cdg_get_dt.argtypes = [vp, dp, dp]
+    L.cdg_rk_stage.restype = st
+    L.cdg_rk_stage.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    L.cdg_oe_damp.restype = st
+    L.cdg_oe_damp.argtypes = [vp, vp, vp]
+    L.cdg_oe_coefficients.restype = st
+    L.cdg_oe_coefficients.argtypes = [vp, vp, vp, vp]
+    L.cdg_step.restype = st
+    L.cdg_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.cdg_step_async.restype = st
+    L.cdg_step_async.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.cdg_get_time.restype = st
+    L.cdg_get_time.argtypes = [vp, dp]
+    L.cdg_check_status.restype = st
+    L.cdg_check_status.argtypes = [vp]
+    L.cdg_launch_count.restype = st
+    L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+@dataclass
+class MeshDesc:
+    dim: int = 2
+    nx: int = 64
+    ny: int = 64
+    k: int = 2
+    basis: int = BASIS_Q
+    system: int = EULER
+    bc: int = PERIODIC
+    oe: int = 1
+    rk: int = RK_SSP3
+    ax: float = 0.0
+    bx: float = 1.0
+    ay: float = 0.0
+    by: float = 1.0
+    gamma: float = 1.4
+    adv_x: float = 1.0
+    adv_y: float = 0.0
+    cfl: float = 0.1
+
+    def c(self) -> cdg_mesh_desc:
+        return cdg_mesh_desc(self.dim, self.nx, self.ny if self.dim == 2 else 1, self.k, self.basis, self.system,
+                             self.bc, self.oe, self.rk, 0, self.ax, self.bx, self.ay, self.by, self.gamma,
+                             self.adv_x, self.adv_y, self.cfl)
+
+    @property
+    def nfields(self) -> int:
+        return self.dim + 2 if self.system == EULER else 1
+
+    @property
+    def nmodes(self) -> int:
+        return 9 if self.dim == 2 else 3
+
+    @property
+    def shape(self):
+        return (2, self.nfields, self.nmodes, self.ny if self.dim == 2 else 1, self.nx)
+
+
+def desc_from_workload(w, **over) -> MeshDesc:
+    d = MeshDesc(dim=w.dim, nx=w.nx, ny=w.ny, k=w.k, basis=w.basis, system=w.system, bc=w.bc, oe=w.oe,
+                 rk=w.rk, ax=w.ax, bx=w.bx, ay=w.ay, by=w.by, gamma=w.gamma, adv_x=w.adv[0], adv_y=w.adv[1],
+                 cfl=w.cfl)
+    for k_, v in over.items():
+        setattr(d, k_, v)
+    return d
+
+
+class Context:
+    """Owner of a cdg_ctx; methods map one-to-one onto the C-ABI calls."""
+
+    def __init__(self, desc: MeshDesc, stream=None):
+        import torch
+        L = load()
+        self.desc = desc
+        self._L = L
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        self._cdesc = desc.c()
+        s = L.cdg_init_mesh(ctypes.byref(self._cdesc), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if s != CDG_OK:
+            raise CdgError(s, "cdg_init_mesh")
+        self.h = h
+
+    def _ck(self, s: int, what: str):
+        if s != CDG_OK:
+            msg = self._L.cdg_last_error(self.h)
+            raise CdgError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._L.cdg_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the C-ABI -------------------------------------------------------
+    def cdg_state_numel(self) -> int:
+        n = ctypes.c_size_t()
+        self._ck(self._L.cdg_state_numel(self.h, ctypes.byref(n)), "cdg_state_numel")
+        return n.value
+
+    def cdg_quad_points(self, d_xy=None) -> int:
+        n = ctypes.c_size_t()
+        self._ck(self._L.cdg_quad_points(self.h, _ptr(d_xy), ctypes.byref(n)), "cdg_quad_points")
+        return n.value
+
+    def cdg_project_ic(self, d_vals, d_u):
+        self._ck(self._L.cdg_project_ic(self.h, _ptr(d_vals), _ptr(d_u)), "cdg_project_ic")
+
+    def cdg_rhs(self, d_u, tau_max: float, d_L):
+        self._ck(self._L.cdg_rhs(self.h, _ptr(d_u), tau_max, _ptr(d_L)), "cdg_rhs")
+
+    def cdg_compute_dt(self, d_u, t: float = 0.0, T_end: float = 0.0):
+        self._ck(self._L.cdg_compute_dt(self.h, _ptr(d_u), t, T_end), "cdg_compute_dt")
+
+    def cdg_set_dt(self, tau: float, tau_max: float):
+        self._ck(self._L.cdg_set_dt(self.h, tau, tau_max), "cdg_set_dt")
+
+    def cdg_get_dt(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._ck(self._L.cdg_get_dt(self.h, ctypes.byref(a), ctypes.byref(b)), "cdg_get_dt")
+        return a.value, b.value
+
+    def cdg_rk_stage(self, l: int, d_un, d_ul, d_out):
+        self._ck(self._L.cdg_rk_stage(self.h, l, _ptr(d_un), _ptr(d_ul), _ptr(d_out)), "cdg_rk_stage")
+
+    def cdg_oe_damp(self, d_uh, d_usig):
+        self._ck(self._L.cdg_oe_damp(self.h, _ptr(d_uh), _ptr(d_usig)), "cdg_oe_damp")
+
+    def cdg_oe_coefficients(self, d_uh, d_delta=None, d_sigma=None):
+        self._ck(self._L.cdg_oe_coefficients(self.h, _ptr(d_uh), _ptr(d_delta), _ptr(d_sigma)),
+                 "cdg_oe_coefficients")
+
+    def cdg_step(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
+        self._ck(self._L.cdg_step(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step")
+
+    def cdg_step_async(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
+        self._ck(self._L.cdg_step_async(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_async")
+
+    def cdg_get_time(self) -> float:
+        t = ctypes.c_double()
+        self._ck(self._L.cdg_get_time(self.h, ctypes.byref(t)), "cdg_get_time")
+        return t.value
+
+    def cdg_check_status(self) -> int:
+        return self._L.cdg_check_status(self.h)
+
+    def cdg_launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        self._ck(self._L.cdg_launch_count(self.h, ctypes.byref(n)), "cdg_launch_count")
+        return n.value
+
+    # ---- conveniences (marshalling only) ----------------------------------
+    def zeros(self):
+        import torch
+        return torch.zeros(self.desc.shape, dtype=torch.float64, device="cuda")
+
+    def project(self, fn):
+        """Sample u0 = fn(xy[npts, dim]) -> [npts, F] at the context's points and project."""
+        import numpy as np
+        import torch
+        n = self.cdg_quad_points(None)
+        xy = torch.empty((n, self.desc.dim), dtype=torch.float64, device="cuda")
+        self.cdg_quad_points(xy)
+        vals = np.ascontiguousarray(fn(xy.cpu().numpy()), dtype=np.float64).reshape(n, self.desc.nfields)
+        dv = torch.from_numpy(vals).cuda()
+        u = self.zeros()
+        self.cdg_project_ic(dv, u)
+        return u

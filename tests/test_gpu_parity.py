@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Metric: relative L1 per field over all modal coefficients of both meshes,
+    sum |u_gpu - u_oracle| / sum |u_oracle|,
+at most 1e-11 on smooth runs and 1e-9 on discontinuous runs after the stated
+step counts; single operator applications (RHS, one stage, OE) at most 1e-12.
+Sizes span several 32 x 4 cell tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_12473_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2503_12473_gb300 import oecdg
+    oecdg.load()  # raises loudly if the library is missing
+
+
+def _ctx(w, **over):
+    from paper_2503_12473_gb300 import oecdg as G
+    return G.Context(G.desc_from_workload(w, **over))
+
+
+def _oracle_problem(w, **over):
+    p = O.Problem(dim=w.dim, nx=w.nx, ny=w.ny, k=w.k, basis=w.basis, system=w.system, bc=w.bc, oe=w.oe, rk=w.rk,
+                  ax=w.ax, bx=w.bx, ay=w.ay, by=w.by, gamma=w.gamma, adv_x=w.adv[0], adv_y=w.adv[1], cfl=w.cfl)
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def rel_l1(a, b):
+    """Per-field relative L1 over both meshes; a, b: [2, F, M, ny, nx]."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).sum(axis=(0, 2, 3, 4))
+    den = np.abs(b).sum(axis=(0, 2, 3, 4))
+    return num / np.maximum(den, 1e-300)
+
+
+def _both_projections(w, **over):
+    ctx = _ctx(w, **over)
+    p = _oracle_problem(w, **over)
+    ug = ctx.project(w.u0)
+    uo = O.project_fn(p, w.u0)
+    return ctx, p, ug, uo
+
+
+SMALL_2D = [
+    ("riemann_trans_40x28", lambda: W.riemann_2d(n=40).resized(40, 28), 1e-9),
+    ("vortex_per_36", lambda: W.vortex_2d(n=36).resized(36, 36), 1e-11),
+]
+
+
+@pytest.mark.parametrize("name,mk,tol", SMALL_2D)
+def test_quad_points_and_projection(name, mk, tol):
+    w = mk()
+    ctx, p, ug, uo = _both_projections(w)
+    n = ctx.cdg_quad_points(None)
+    xy = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    ctx.cdg_quad_points(xy)
+    np.testing.assert_allclose(xy.cpu().numpy(), O.quad_points(p), rtol=0, atol=1e-14)
+    assert rel_l1(ug.cpu().numpy(), uo).max() < 1e-13
+
+
+def _perturbed(w, seed, amp=1e-2, **over):
+    """Projected data plus a seeded perturbation of every modal coefficient
+    (keeps rho and p positive), identical on both sides."""
+    ctx, p, ug, uo = _both_projections(w, **over)
+    pert = W.perturbation(uo.shape, seed, amp)
+    pert[:, 0] *= 0.5
+    # each side perturbs its own projection (they agree to round-off)
+    return ctx, p, ug + torch.from_numpy(pert).cuda(), uo + pert
+
+
+@pytest.mark.parametrize("name,mk,tol", SMALL_2D)
+def test_rhs_parity_2d(name, mk, tol):
+    w = mk()
+    ctx, p, ug, uo = _perturbed(w, 7)
+    tm = 3.7e-3
+    Lg = torch.empty_like(ug)
+    ctx.cdg_rhs(ug, tm, Lg)
+    Lo = O.rhs(p, uo, tm)
+    assert rel_l1(Lg.cpu().numpy(), Lo).max() < 1e-12
+
+
+def test_rhs_parity_2d_advection():
+    w = W.Workload("adv2d", 2, 37, 30, 2, W.ADVECTION, W.PERIODIC, 0.0, 1.0, 0.0, 1.2, adv=(0.7, -1.3),
+                   u0=lambda xy: (np.sin(2 * np.pi * xy[:, 0]) * np.cos(2 * np.pi * xy[:, 1] / 1.2))[:, None])
+    ctx, p, ug, uo = _perturbed(w, 9, 0.1)
+    Lg = torch.empty_like(ug)
+    ctx.cdg_rhs(ug, 0.01, Lg)
+    assert rel_l1(Lg.cpu().numpy(), O.rhs(p, uo, 0.01)).max() < 1e-12
+
+
+@pytest.mark.parametrize("name,mk,tol", SMALL_2D)
+def test_oe_coefficients_parity_2d(name, mk, tol):
+    w = mk()
+    ctx, p, ug, uo = _perturbed(w, 11)
+    ny = w.ny
+    dg = torch.zeros((2, ny, w.nx, 3), dtype=torch.float64, device="cuda")
+    sg = torch.zeros((2, w.nfields), dtype=torch.float64, device="cuda")
+    ctx.cdg_oe_coefficients(ug, dg, sg)
+    do, so, ao, st = O.oe_coefficients(p, uo)
+    # avg is a sum over ~10^4 cell values in a different order on each side:
+    # the rounding bound n * eps relative to max |u| is ~1e-12
+    np.testing.assert_allclose(sg.cpu().numpy(), so, rtol=1e-11)
+    d = dg.cpu().numpy()
+    assert np.abs(d - do).sum() / np.abs(do).sum() < 1e-12
+    assert np.abs(d - do).max() <= 1e-11 * np.abs(do).max()
+
+
+@pytest.mark.parametrize("name,mk,tol", SMALL_2D)
+def test_stage_and_oe_parity_2d(name, mk, tol):
+    """cdg_rk_stage (each SSP-RK3 stage) and cdg_oe_damp against the oracle's
+    stage combination and OE step, with the same (tau, tau_max)."""
+    w = mk()
+    ctx, p, ug, uo = _perturbed(w, 13)
+    tm, _ = O.tau_max(p, uo)
+    ctx.cdg_set_dt(tm, tm)
+    for l, (ca, cb) in enumerate([(0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)]):
+        ul = uo * (1 + 0.01 * l)
+        ref = ca * uo + cb * (ul + tm * O.rhs(p, ul, tm))
+        out = torch.empty_like(ug)
+        ctx.cdg_rk_stage(l, ug, ug * (1 + 0.01 * l), out)
+        assert rel_l1(out.cpu().numpy(), ref).max() < 1e-12
+    # OE step of each side's own first stage
+    u1g = torch.empty_like(ug)
+    ctx.cdg_rk_stage(0, ug, ug, u1g)
+    u1o = uo + tm * O.rhs(p, uo, tm)
+    out = torch.empty_like(ug)
+    ctx.cdg_oe_damp(u1g, out)
+    ref, st = O.oe(p, u1o, tm)
+    assert rel_l1(out.cpu().numpy(), ref).max() < 1e-11
+
+
+@pytest.mark.parametrize("name,mk,tol,steps", [(n, m, t, 6) for n, m, t in SMALL_2D])
+def test_step_parity_2d(name, mk, tol, steps):
+    """cdg_step (the full hot path: wave speed, three stages each with the OE
+    step) against the oracle after several steps."""
+    w = mk()
+    ctx, p, ug, uo = _both_projections(w)
+    ctx.cdg_step(ug, 0.0, 0.0, steps)
+    ref, t, n, st = O.advance(p, uo, 0.0, 0.0, steps)
+    assert st == O.OK
+    err = rel_l1(ug.cpu().numpy(), ref)
+    assert err.max() < tol, err
+    tg = ctx.cdg_get_time()
+    assert abs(tg - t) <= 1e-14 * max(t, 1.0)
+
+
+def test_step_parity_1d_advection():
+    """1D advection of sin x, P^2, SSP-RK3, CFL 0.1 (128 cells): 200 steps."""
+    w = W.advection_1d(128)
+    ctx, p, ug, uo = _both_projections(w)
+    ctx.cdg_step(ug, 0.0, w.T, 200)
+    ref, t, n, st = O.advance(p, uo, 0.0, w.T, 200)
+    assert rel_l1(ug.cpu().numpy(), ref).max() < 1e-11
+
+
+def test_step_parity_1d_shu_osher():
+    """1D Euler, Shu-Osher data, transmissive, P^2 (400 cells): 100 steps."""
+    w = W.shu_osher_1d(400)
+    ctx, p, ug, uo = _both_projections(w)
+    ctx.cdg_step(ug, 0.0, w.T, 100)
+    ref, t, n, st = O.advance(p, uo, 0.0, w.T, 100)
+    assert st == O.OK
+    assert rel_l1(ug.cpu().numpy(), ref).max() < 1e-9
+
+
+def test_rhs_and_oe_parity_1d():
+    w = W.shu_osher_1d(333)
+    ctx, p, ug, uo = _perturbed(w, 17, 1e-3)
+    Lg = torch.empty_like(ug)
+    ctx.cdg_rhs(ug, 1e-3, Lg)
+    assert rel_l1(Lg.cpu().numpy(), O.rhs(p, uo, 1e-3)).max() < 1e-12
+    dg = torch.zeros((2, 1, w.nx, 3), dtype=torch.float64, device="cuda")
+    ctx.cdg_oe_coefficients(ug, dg, None)
+    do, so, ao, st = O.oe_coefficients(p, uo)
+    d = dg.cpu().numpy()
+    assert np.abs(d - do).max() <= 1e-11 * np.abs(do).max()
+
+
+def test_constant_state_and_edge_sizes():
+    """Degenerate cases: the smallest mesh (2 x 2), a constant state (L = 0,
+    delta = 0, the step is the identity), and one-cell-wide ragged tiles."""
+    for nx, ny in ((2, 2), (33, 5), (3, 129)):
+        w = W.riemann_2d(n=nx).resized(nx, ny)
+        ctx = _ctx(w)
+        u = ctx.zeros()
+        st = torch.tensor([1.3, 0.4, -0.2, 2.9], dtype=torch.float64, device="cuda")
+        u[:, :, 0] = st[None, :, None, None]
+        u0 = u.clone()
+        ctx.cdg_step(u, 0.0, 0.0, 2)
+        assert torch.abs(u - u0).max().item() < 1e-13
+        # the Riemann data on these coarse meshes: both sides must agree on the
+        # status (the 3 x 129 mesh reaches a non-physical cell average) and,
+        # when physical, on the values
+        from paper_2503_12473_gb300 import oecdg as G
+        p = _oracle_problem(w)
+        up = O.project_fn(p, w.u0)
+        ug = ctx.project(w.u0)
+        ref, _, _, st_o = O.advance(p, up, 0.0, 0.0, 2)
+        try:
+            ctx.cdg_step(ug, 0.0, 0.0, 2)
+            st_g = G.CDG_OK
+        except G.CdgError as e:
+            st_g = e.status
+        assert st_g == {O.OK: G.CDG_OK, O.ENONPHYSICAL: G.CDG_ENONPHYSICAL}[st_o], (nx, ny, st_g, st_o)
+        if st_o == O.OK:
+            assert rel_l1(ug.cpu().numpy(), ref).max() < 1e-9
+
+
+def test_nonphysical_state_is_reported():
+    """A negative density in a cell average is reported as CDG_ENONPHYSICAL
+    (set on the host; the kernels raise a status flag, nothing faults)."""
+    from paper_2503_12473_gb300 import oecdg as G
+    w = W.riemann_2d(n=16)
+    ctx = _ctx(w)
+    u = ctx.project(w.u0)
+    u[0, 0, 0, 3, 5] = -1.0
+    with pytest.raises(G.CdgError) as e:
+        ctx.cdg_step(u, 0.0, 0.0, 1)
+    assert e.value.status == G.CDG_ENONPHYSICAL
+
+
+def test_invalid_arguments():
+    from paper_2503_12473_gb300 import oecdg as G
+    with pytest.raises(G.CdgError) as e:
+        G.Context(G.MeshDesc(dim=2, nx=1, ny=8))
+    assert e.value.status == G.CDG_EINVAL
+    with pytest.raises(G.CdgError) as e:
+        G.Context(G.MeshDesc(dim=2, nx=8, ny=8, k=3))
+    assert e.value.status == G.CDG_EUNSUPPORTED
+    ctx = G.Context(G.MeshDesc(dim=2, nx=8, ny=8))
+    u = ctx.zeros()
+    with pytest.raises(G.CdgError):
+        ctx.cdg_rhs(u, 1e-3, u)
