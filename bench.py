@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the OECDG forward step (arXiv:2503.12473) on GB300.
+
+Workload: 2D Euler (gamma = 1.4) OECDG, Q^2 tensor Legendre basis, 1024 x 1024
+primal mesh + dual mesh shifted by (h/2, h/2), [0,1]^2 transmissive, SSP-RK3,
+CFL 0.1, four-quadrant Riemann data split at (0.8, 0.8) (synthetic, seeded-free
+closed-form data).  A "step" is one SSP-RK3 time step: the wave-speed
+reduction, then three stages of (CDG right-hand side + RK combine, sigma
+reduction, OE damping).
+
+Metric: FP64 DOF-updates per second per RK stage = 3 * DOF * steps / time,
+DOF = 2 meshes x 4 fields x 9 modes x 1024^2 = 75,497,472.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun); the
+value is the sum over ranks of the work divided by the max over ranks of the
+time.  The reference arm times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 DOF-updates/s per RK stage, 2D Euler 1024^2 k=2"
+UNIT = "DOF-updates/s"
+
+# Peaks (per GPU).  HBM: the measured copy bandwidth of the GB300s.
+# FP64: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz (the nominal
+# 1.25 TFLOP/s at the maximum SM clock); a DFMA-throughput probe measured 1.19
+# TFLOP/s at 1.99 GHz, i.e. the same 2 FMA per SM per clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+# Algorithmic FP64 flops per cell (one primal or dual cell, 2D Euler Q^2) of
+# the two hot kernels, counted from the executed FP64 instructions of one
+# launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
+# kernels are branch-free and fully unrolled, so this is the arithmetic of the
+# algorithm as implemented.  Source: profiles/fp64_counts_euler2d_q2.md.
+FLOPS_PER_CELL = {"stage": 7472, "oe": 8532}
+# DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
+# once a kernel changes after the capture.
+TRAFFIC_PER_CELL = {"stage": 859, "oe": 809}
+# Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
+# three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
+# (neighbour re-reads are L2 hits).
+BYTES_PER_CELL = {"stage": (36 + 24 + 36) * 8, "oe": (36 + 36) * 8}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        sm_sorted = sorted(sm)
+        med = sm_sorted[len(sm_sorted) // 2] if sm_sorted else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def init_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def config_dict(n, dof):
+    return {"workload": f"euler_2d_riemann_q2_{n}", "model": None, "nx": n, "ny": n, "k": 2, "basis": "Q",
+            "system": "euler", "bc": "transmissive", "rk": "ssp-rk3", "cfl": 0.1, "oe": True, "dof": dof,
+            "l2": "inputs larger than L2 (state 604 MB > 129 MB L2)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- oracle ---
+
+def oracle_rate(steps: int, warmup: int, budget_s: float = 90.0):
+    """Time the CPU oracle on the same workload at a bounded mesh size.  Returns
+    (DOF-updates/s, cores, sample text, seconds per step)."""
+    from oracle import oracle as O
+    from paper_2503_12473_gb300 import workloads as W
+    cores = O.num_threads()
+
+    def run(n, k):
+        w = W.riemann_2d(n=n)
+        p = O.Problem(dim=2, nx=n, ny=n, k=2, system=O.EULER, bc=O.TRANSMISSIVE, cfl=0.1)
+        u = O.project_fn(p, w.u0)
+        t0 = time.perf_counter()
+        O.advance(p, u, 0.0, 0.0, k)
+        return time.perf_counter() - t0, u.size
+
+    dt, dof = run(16, 1)
+    rate = 3 * dof / dt
+    per_step = budget_s / max(steps + warmup, 1)
+    n = int(math.sqrt(per_step * rate / (3 * 72)))
+    n = max(8, min(128, (n // 8) * 8))
+    if warmup:
+        run(n, warmup)
+    dt, dof = run(n, steps)
+    rate = 3 * dof * steps / dt
+    sample = (f"four-quadrant Riemann data on a {n}x{n} Q^2 mesh (same workload, smaller mesh: the oracle's cost "
+              f"per DOF-update does not depend on the mesh size), {steps} SSP-RK3 steps after {warmup} warm-up")
+    return rate, cores, sample, dt / steps
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    steps, warmup = args.steps, args.warmup
+    rate, cores, sample, sps = oracle_rate(steps, warmup)
+    dof = 2 * 4 * 9 * args.n * args.n
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": warmup, "ms_per_step": sps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args.n, dof),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours ---
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2503_12473_gb300 import oecdg as G
+    from paper_2503_12473_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    G.load()
+    n = args.n
+    w = W.riemann_2d(n=n)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w), stream=stream)
+    dof = ctx.cdg_state_numel()
+    with torch.cuda.stream(stream):
+        u0 = ctx.project(w.u0)
+        # warm-up on a copy
+        uw = u0.clone()
+        if args.warmup:
+            ctx.cdg_step_async(uw, 0.0, 0.0, args.warmup)
+        stream.synchronize()
+        st = ctx.cdg_check_status()
+        if st != G.CDG_OK:
+            raise G.CdgError(st, "warm-up")
+        del uw
+        u = u0.clone()
+        stream.synchronize()
+
+        def barrier():
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        launches0 = ctx.cdg_launch_count()
+        ctx.cdg_profile_begin(3 * args.steps + 8)
+        barrier()
+        ev0.record(stream)
+        ctx.cdg_step_async(u, 0.0, 0.0, args.steps)
+        ev1.record(stream)
+        barrier()
+        clocks_res = clocks.stop()
+        prof = ctx.cdg_profile_end()
+        launches = ctx.cdg_launch_count() - launches0
+        ms = ev0.elapsed_time(ev1)
+        st = ctx.cdg_check_status()
+        if st != G.CDG_OK:
+            raise G.CdgError(st, "timed steps")
+        t_final = ctx.cdg_get_time()
+        ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        ms_max = ms_t.item()
+        value = 3.0 * dof * args.steps * ws / (ms_max * 1e-3)
+
+        # end to end through the C-ABI with host buffers: each step copies the
+        # state from pinned host memory, steps, and copies the result back
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        h_u = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
+        h_u.copy_(u0)
+        d_u = torch.empty_like(u0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            d_u.copy_(h_u, non_blocking=True)
+            ctx.cdg_step_async(d_u, 0.0, 0.0, 1)
+            h_u.copy_(d_u, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_value = 3.0 * dof * e2e_steps * ws / (e2e_t.item() * 1e-3)
+        state_bytes = dof * 8
+
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel, from the events of the timed region
+    cells = 2 * n * n
+    kname = "stage" if prof["stage"][0] >= prof["oe"][0] else "oe"
+    kms, kcount = prof[kname]
+    avg_s = (kms / max(kcount, 1)) * 1e-3
+    fpc = FLOPS_PER_CELL[kname]
+    peaks = measured_peaks()
+    roof = {"bound": "alu", "kernel": f"k_{kname}2d (Euler, transmissive)", "unit": "TFLOP/s",
+            "peak": FP64_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+            "avg_launch_ms": avg_s * 1e3, "launches": kcount,
+            "traffic": (TRAFFIC_PER_CELL[kname] * cells if TRAFFIC_PER_CELL[kname] is not None else None),
+            "traffic_unit": "bytes per launch"}
+    if fpc is not None:
+        roof["achieved"] = fpc * cells / avg_s / 1e12
+        roof["frac"] = roof["achieved"] / FP64_PEAK_TFLOPS
+        roof["flops_per_cell"] = fpc
+    else:
+        roof["achieved"] = None
+        roof["frac"] = None
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    roof["hbm"] = {"achieved_gbs": BYTES_PER_CELL[kname] * cells / avg_s / 1e9, "peak_gbs": hbm_peak,
+                   "frac": BYTES_PER_CELL[kname] * cells / avg_s / 1e9 / hbm_peak,
+                   "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    roof["kernel_share"] = {k: prof[k][0] / ms for k in ("stage", "oe")}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(n, dof),
+            "t_final": t_final, "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},
+            "gpu_launches": launches, "clocks": clocks_res}
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, sps = oracle_rate(2, 0, budget_s=20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="cells per direction (the workload is 1024)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    ws, rank, local = init_dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,15 @@ cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
  * CDG_ENONPHYSICAL. */
 cdg_status cdg_check_status(cdg_ctx* ctx);
 
+/* Optional per-kernel timing: between cdg_profile_begin and cdg_profile_end,
+ * every stage kernel (CDG RHS + RK combine) and every OE kernel launched by the
+ * context is bracketed by CUDA events on the context's stream (at most
+ * max_launches of each).  cdg_profile_end synchronises and returns the summed
+ * event durations (ms) and the launch counts of the two kernel classes (any
+ * pointer may be NULL).  Not for use inside a CUDA graph capture. */
+cdg_status cdg_profile_begin(cdg_ctx* ctx, int max_launches);
+cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, double* ms_oe, long long* n_oe);
+
 /* Number of kernels launched by the context so far (host-side counter). */
 cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
 

@@ -33,8 +33,34 @@ struct cdg_ctx {
   double* avg;           // [2][F]
   int* status;           // status bits
   long long launches;
+  // optional per-kernel timing (cdg_profile_begin / cdg_profile_end)
+  int prof_on;
+  int prof_cap;
+  int prof_n[2];
+  cudaEvent_t* prof_ev[2];  // [class][2 * cap]: start, stop
   char err[256];
 };
+
+enum { PROF_STAGE = 0, PROF_OE = 1 };
+
+static void prof_mark(cdg_ctx* c, int cls, int stop) {
+  if (!c->prof_on) return;
+  const int n = c->prof_n[cls];
+  if (n >= c->prof_cap) return;
+  cudaEventRecord(c->prof_ev[cls][2 * n + stop], c->stream);
+  if (stop) c->prof_n[cls] = n + 1;
+}
+
+static void prof_release(cdg_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    if (!c->prof_ev[k]) continue;
+    for (int q = 0; q < 2 * c->prof_cap; ++q) cudaEventDestroy(c->prof_ev[k][q]);
+    free(c->prof_ev[k]);
+    c->prof_ev[k] = nullptr;
+  }
+  c->prof_cap = 0;
+  c->prof_on = 0;
+}
 
 static cdg_status fail(cdg_ctx* c, cdg_status s, const char* msg) {
   if (c) snprintf(c->err, sizeof c->err, "%s", msg);
@@ -136,6 +162,7 @@ cdg_status cdg_free(cdg_ctx* c) {
   cudaFree(c->sigma);
   cudaFree(c->avg);
   cudaFree(c->status);
+  prof_release(c);
   free(c);
   return CDG_OK;
 }
@@ -179,9 +206,14 @@ static cudaError_t run_stage(cdg_ctx* ctx, int rhs_only, const double* uin, cons
   const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
   const int bc = ctx->d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
   ctx->launches += 1;
+  prof_mark(ctx, PROF_STAGE, 0);
+  cudaError_t e;
   if (ctx->d.dim == 2)
-    return launch_stage2d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
-  return launch_stage1d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+    e = launch_stage2d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+  else
+    e = launch_stage1d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+  prof_mark(ctx, PROF_STAGE, 1);
+  return e;
 }
 
 // sigma from the partials of the last stage kernel, then the OE kernel
@@ -191,9 +223,13 @@ static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* 
   cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
+  prof_mark(ctx, PROF_OE, 0);
   if (ctx->d.dim == 2)
-    return launch_oe2d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
-  return launch_oe1d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+    e = launch_oe2d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+  else
+    e = launch_oe1d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+  prof_mark(ctx, PROF_OE, 1);
+  return e;
 }
 
 cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L) {
@@ -330,6 +366,48 @@ cdg_status cdg_check_status(cdg_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "check_status");
   CK(cudaStreamSynchronize(ctx->stream), "check_status");
   if (h & ST_NONPHYSICAL) return fail(ctx, CDG_ENONPHYSICAL, "non-physical cell average (rho <= 0 or p <= 0)");
+  return CDG_OK;
+}
+
+cdg_status cdg_profile_begin(cdg_ctx* ctx, int max_launches) {
+  if (!ctx || max_launches < 1) return CDG_EINVAL;
+  prof_release(ctx);
+  for (int k = 0; k < 2; ++k) {
+    ctx->prof_ev[k] = (cudaEvent_t*)calloc((size_t)2 * max_launches, sizeof(cudaEvent_t));
+    if (!ctx->prof_ev[k]) {
+      prof_release(ctx);
+      return CDG_ENOMEM;
+    }
+  }
+  ctx->prof_cap = max_launches;
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < 2 * max_launches; ++q) {
+      cudaError_t e = cudaEventCreate(&ctx->prof_ev[k][q]);
+      if (e != cudaSuccess) {
+        prof_release(ctx);
+        return cuda_fail(ctx, e, "profile_begin");
+      }
+    }
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
+  ctx->prof_on = 1;
+  return CDG_OK;
+}
+
+cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, double* ms_oe, long long* n_oe) {
+  if (!ctx || !ctx->prof_on) return CDG_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream), "profile_end");
+  double tot[2] = {0.0, 0.0};
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < ctx->prof_n[k]; ++q) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->prof_ev[k][2 * q], ctx->prof_ev[k][2 * q + 1]), "profile_end");
+      tot[k] += ms;
+    }
+  if (ms_stage) *ms_stage = tot[0];
+  if (n_stage) *n_stage = ctx->prof_n[0];
+  if (ms_oe) *ms_oe = tot[1];
+  if (n_oe) *n_oe = ctx->prof_n[1];
+  prof_release(ctx);
   return CDG_OK;
 }
 

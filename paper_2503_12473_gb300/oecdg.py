@@ -28,6 +28,7 @@ EXPORTED = [
     "cdg_init_mesh", "cdg_free", "cdg_last_error", "cdg_state_numel", "cdg_quad_points", "cdg_project_ic",
     "cdg_rhs", "cdg_compute_dt", "cdg_set_dt", "cdg_get_dt", "cdg_rk_stage", "cdg_oe_damp",
     "cdg_oe_coefficients", "cdg_step", "cdg_step_async", "cdg_get_time", "cdg_check_status", "cdg_launch_count",
+    "cdg_profile_begin", "cdg_profile_end",
 ]
 
 
@@ -102,6 +103,11 @@ def load(build_if_missing: bool = True):
     L.cdg_get_time.argtypes = [vp, dp]
     L.cdg_check_status.restype = st
     L.cdg_check_status.argtypes = [vp]
+    L.cdg_profile_begin.restype = st
+    L.cdg_profile_begin.argtypes = [vp, ctypes.c_int]
+    L.cdg_profile_end.restype = st
+    L.cdg_profile_end.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), dp,
+                                  ctypes.POINTER(ctypes.c_longlong)]
     L.cdg_launch_count.restype = st
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     _lib = L
@@ -257,6 +263,17 @@ class Context:
         n = ctypes.c_longlong()
         self._ck(self._L.cdg_launch_count(self.h, ctypes.byref(n)), "cdg_launch_count")
         return n.value
+
+    def cdg_profile_begin(self, max_launches: int):
+        self._ck(self._L.cdg_profile_begin(self.h, max_launches), "cdg_profile_begin")
+
+    def cdg_profile_end(self):
+        """Returns {'stage': (ms_total, launches), 'oe': (ms_total, launches)}."""
+        a, c = ctypes.c_double(), ctypes.c_double()
+        b, d = ctypes.c_longlong(), ctypes.c_longlong()
+        self._ck(self._L.cdg_profile_end(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(d)), "cdg_profile_end")
+        return {"stage": (a.value, b.value), "oe": (c.value, d.value)}
 
     # ---- conveniences (marshalling only) ----------------------------------
     def zeros(self):
