@@ -163,6 +163,40 @@ cdg_status cdg_check_status(cdg_ctx* ctx);
 cdg_status cdg_profile_begin(cdg_ctx* ctx, int max_launches);
 cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, double* ms_oe, long long* n_oe);
 
+/* The OE step of cdg_oe_damp for callers that cannot allocate device memory.
+ *
+ * Some callers cannot call cudaMalloc: code embedded in a host application
+ * whose memory manager owns the whole device heap (a direct allocation would
+ * be refused or fragment it), or a latency-critical path that must not
+ * allocate, nor wait on an allocation, once it is running.  This entry point
+ * needs no context and allocates nothing.  Its scratch (sigma partials, sigma
+ * and avg, tau and a status word) is a 1 MiB array compiled into the library's
+ * device image, so every GPU that loads the library holds it until the process
+ * exits.  The paper has no counterpart: this is an interface for such callers,
+ * not a step of the method.
+ *
+ * desc:   mesh description, same rules as cdg_init_mesh.
+ * d_uh:   device state to damp (input, caller-owned); d_usig: device state
+ *         (output, caller-owned, must not alias d_uh); both cdg_state_numel()
+ *         doubles in the layout above.
+ * tau:    damping time (>= 0), the t_hat = tau of Eq. (OEstep2D).
+ * stream: a cudaStream_t (NULL = the legacy default stream); asynchronous.
+ * Limit:  the partials need 2 * ceil(cells per mesh / 256) * fields * 3
+ *         doubles of the 131,008 available: at most 1,397,248 cells per mesh
+ *         with 4 fields (2D Euler; 1024 x 1024 fits), 1,863,168 with 3 (1D
+ *         Euler), 5,589,504 with 1 (advection).  Larger meshes return
+ *         CDG_EINVAL without launching anything.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the one array and overwrites or clears
+ * what it uses, so calls that overlap on the GPU (two streams, or two host
+ * threads) race: the caller must order them.  Non-physical cell averages are
+ * not reported by this entry point (their wave speed is taken as 0).
+ * Errors: CDG_EINVAL (bad pointers or sizes, aliasing, tau < 0, mesh beyond the
+ * limit), CDG_EUNSUPPORTED (as cdg_init_mesh), CDG_ECUDA. */
+cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const double* d_uh, double tau, double* d_usig,
+                               void* stream);
+
 /* Number of kernels launched by the context so far (host-side counter). */
 cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
 

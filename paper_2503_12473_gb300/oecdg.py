@@ -28,7 +28,7 @@ EXPORTED = [
     "cdg_init_mesh", "cdg_free", "cdg_last_error", "cdg_state_numel", "cdg_quad_points", "cdg_project_ic",
     "cdg_rhs", "cdg_compute_dt", "cdg_set_dt", "cdg_get_dt", "cdg_rk_stage", "cdg_oe_damp",
     "cdg_oe_coefficients", "cdg_step", "cdg_step_async", "cdg_get_time", "cdg_check_status", "cdg_launch_count",
-    "cdg_profile_begin", "cdg_profile_end",
+    "cdg_profile_begin", "cdg_profile_end", "cdg_oe_damp_noalloc",
 ]
 
 
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
     L.cdg_profile_end.restype = st
     L.cdg_profile_end.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), dp,
                                   ctypes.POINTER(ctypes.c_longlong)]
+    L.cdg_oe_damp_noalloc.restype = st
+    L.cdg_oe_damp_noalloc.argtypes = [ctypes.POINTER(cdg_mesh_desc), vp, ctypes.c_double, vp, vp]
     L.cdg_launch_count.restype = st
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     _lib = L
@@ -171,6 +173,18 @@ def desc_from_workload(w, **over) -> MeshDesc:
     for k_, v in over.items():
         setattr(d, k_, v)
     return d
+
+
+def cdg_oe_damp_noalloc(desc: MeshDesc, d_uh, tau: float, d_usig, stream=None) -> None:
+    """The context-free, allocation-free OE step (see include/oecdg.h)."""
+    import torch
+    L = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    cd = desc.c()
+    s = L.cdg_oe_damp_noalloc(ctypes.byref(cd), _ptr(d_uh), tau, _ptr(d_usig), ctypes.c_void_p(stream.cuda_stream))
+    if s != CDG_OK:
+        raise CdgError(s, "cdg_oe_damp_noalloc")
 
 
 class Context:
