@@ -11,7 +11,16 @@
 
 namespace oecdg {
 
-constexpr int TX = 32, TY = 4, NT = TX * TY;  // cell tile of one block
+#ifndef OECDG_TY
+#define OECDG_TY 4
+#endif
+#ifndef OECDG_STAGE_MINB
+#define OECDG_STAGE_MINB 1
+#endif
+#ifndef OECDG_OE_MINB
+#define OECDG_OE_MINB 1
+#endif
+constexpr int TX = 32, TY = OECDG_TY, NT = TX * TY;  // cell tile of one block
 constexpr double DINF = __builtin_huge_val();
 
 template <int SYS>
@@ -219,7 +228,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
 enum { MODE_RHS = 0, MODE_STAGE = 1 };
 
 template <int SYS, int BC, int MODE>
-__global__ void __launch_bounds__(NT) k_stage2d(Geo g, const double* __restrict__ uin,
+__global__ void __launch_bounds__(NT, OECDG_STAGE_MINB) k_stage2d(Geo g, const double* __restrict__ uin,
                                                 const double* __restrict__ un, double* __restrict__ out,
                                                 const double* __restrict__ dt, double ca, double cb,
                                                 double* __restrict__ partials) {
@@ -322,7 +331,7 @@ __global__ void k_sigma(const double* __restrict__ partials, long long nblk, int
 // over fields (Remark on systems); delta = 0 where sigma = 0.  Mode (a,b) then
 // decays by exp(-tau sum_{m <= min(a+b, 2)} delta^m), the average is kept.
 template <int SYS, int BC, bool WRITE_DELTA>
-__global__ void __launch_bounds__(NT) k_oe2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
+__global__ void __launch_bounds__(NT, OECDG_OE_MINB) k_oe2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                              const double* __restrict__ dt, const double* __restrict__ sigma,
                                              double* __restrict__ delta_out, int* __restrict__ status) {
   constexpr int F = Fields<SYS>::F;
@@ -361,7 +370,6 @@ __global__ void __launch_bounds__(NT) k_oe2d(Geo g, const double* __restrict__ u
   const double cx0 = 1.0 / (12.0 * g.hx), cx1 = 0.25, cx2 = 5.0 * g.hx / 24.0;
   const double cy0 = 1.0 / (12.0 * g.hy), cy1 = 0.25, cy2 = 5.0 * g.hy / 24.0;
   const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;  // reference -> physical derivative
-  const double dx2 = dx1 * dx1, dy2 = dy1 * dy1, dxy = dx1 * dy1;
 
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;  // max over fields
 #pragma unroll
@@ -372,86 +380,91 @@ __global__ void __launch_bounds__(NT) k_oe2d(Geo g, const double* __restrict__ u
 #pragma unroll
     for (int m = 0; m < 9; ++m) u[m] = __ldg(cs + m * P);
     double Sx0 = 0.0, Sx1 = 0.0, Sx2 = 0.0, Sy0 = 0.0, Sy1 = 0.0, Sy2 = 0.0;
-    // ---- faces normal to x (xi = s), overlapping cells at xi' = 0
+    // Faces normal to direction n (0: x, 1: y), at reference coordinate s of K.
+    // Along the face, K's trace and its normal derivatives of order 0, 1, 2 are
+    // Legendre series c0, c1, c2 in the tangential coordinate t; the overlapping
+    // cell's are o0, o1, o2 in its own tangential coordinate t' = t + dl,
+    // dl = 1 - 2 h (h = the half), re-expanded in t with
+    //   P_1(t + dl) = P_1(t) + dl,  P_2(t + dl) = P_2(t) + 3 dl P_1(t) + 3/2.
+    // The difference series (u_K - w) is then scaled to physical derivatives
+    // and evaluated at the half-face's Gauss points.
 #pragma unroll
-    for (int sx = 0; sx < 2; ++sx) {
-      const double s = 2.0 * sx - 1.0;
-      // self trace along the face: c_ax[b] = sum_a u_ab P_a^{(ax)}(s)
-      double c0[3], c1[3], c2[3];
+    for (int n = 0; n < 2; ++n) {
+      const double dn1 = n == 0 ? dx1 : dy1, dt1 = n == 0 ? dy1 : dx1;  // normal / tangential scales
+      const double dn2 = dn1 * dn1, dt2 = dt1 * dt1;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        c0[b] = u[b * 3] + s * u[b * 3 + 1] + u[b * 3 + 2];
-        c1[b] = fma(3.0 * s, u[b * 3 + 2], u[b * 3 + 1]);
-        c2[b] = 3.0 * u[b * 3 + 2];
-      }
-      const int oi = sx ? oi1 : oi0;
+      for (int side = 0; side < 2; ++side) {
+        const double s = 2.0 * side - 1.0;
+        double c0[3], c1[3], c2[3];
 #pragma unroll
-      for (int sy = 0; sy < 2; ++sy) {
-        const double* co = uo + f * 9 * P + (long long)(sy ? oj1 : oj0) * g.nx + oi;
-        double o0[3], o1[3], o2[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const double w0 = __ldg(co + (b * 3) * P), w1 = __ldg(co + (b * 3 + 1) * P), w2 = __ldg(co + (b * 3 + 2) * P);
-          o0[b] = fma(-0.5, w2, w0);
-          o1[b] = w1;
-          o2[b] = 3.0 * w2;
+        for (int t = 0; t < 3; ++t) {
+          // coefficient (normal degree a, tangential degree t)
+          const double u0 = n == 0 ? u[t * 3] : u[t], u1 = n == 0 ? u[t * 3 + 1] : u[3 + t];
+          const double u2 = n == 0 ? u[t * 3 + 2] : u[6 + t];
+          c0[t] = u0 + s * u1 + u2;
+          c1[t] = fma(3.0 * s, u2, u1);
+          c2[t] = 3.0 * u2;
         }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double es = xs_self(sy, q), eo = xs_other(sy, q);
-          // D_{ax,ay}: x-derivative order ax, y-derivative order ay
-          const double D00 = (c0[0] + es * c0[1] + lp(2, es) * c0[2]) - (o0[0] + eo * o0[1] + lp(2, eo) * o0[2]);
-          const double D10 = (c1[0] + es * c1[1] + lp(2, es) * c1[2]) - (o1[0] + eo * o1[1] + lp(2, eo) * o1[2]);
-          const double D20 = (c2[0] + es * c2[1] + lp(2, es) * c2[2]) - (o2[0] + eo * o2[1] + lp(2, eo) * o2[2]);
-          const double D01 = (c0[1] + 3.0 * es * c0[2]) - (o0[1] + 3.0 * eo * o0[2]);
-          const double D11 = (c1[1] + 3.0 * es * c1[2]) - (o1[1] + 3.0 * eo * o1[2]);
-          const double D02 = 3.0 * (c0[2] - o0[2]);
-          const double e1x = dx1 * D10, e1y = dy1 * D01;
-          const double e2x = dx2 * D20, e2m = dxy * D11, e2y = dy2 * D02;
-          Sx0 = fma(gwt(q), fabs(D00), Sx0);
-          Sx1 = fma(gwt(q), sqrt(fma(e1x, e1x, e1y * e1y)), Sx1);
-          Sx2 = fma(gwt(q), sqrt(fma(e2x, e2x, fma(e2m, e2m, e2y * e2y))), Sx2);
-        }
-      }
-    }
-    // ---- faces normal to y (eta = s), overlapping cells at eta' = 0
+        for (int h = 0; h < 2; ++h) {
+          const double dl = 1.0 - 2.0 * h;
+          const int oi = n == 0 ? (side ? oi1 : oi0) : (h ? oi1 : oi0);
+          const int oj = n == 0 ? (h ? oj1 : oj0) : (side ? oj1 : oj0);
+          const double* co = uo + f * 9 * P + (long long)oj * g.nx + oi;
+          double w0[3], w1[3], w2[3];
 #pragma unroll
-    for (int sy = 0; sy < 2; ++sy) {
-      const double s = 2.0 * sy - 1.0;
-      // self trace along the face: c_ay[a] = sum_b u_ab P_b^{(ay)}(s)
-      double c0[3], c1[3], c2[3];
+          for (int t = 0; t < 3; ++t) {
+            w0[t] = __ldg(co + (n == 0 ? t * 3 : t) * P);
+            w1[t] = __ldg(co + (n == 0 ? t * 3 + 1 : 3 + t) * P);
+            w2[t] = __ldg(co + (n == 0 ? t * 3 + 2 : 6 + t) * P);
+          }
+          // overlapping trace at its centre line (normal coordinate 0)
+          const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
+          const double* o1 = w1;
+          const double o2[3] = {3.0 * w2[0], 3.0 * w2[1], 3.0 * w2[2]};
+          // difference series in K's tangential coordinate
+          double e0[3], e1[3], e2[3];
+          e0[2] = c0[2] - o0[2];
+          e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
+          e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
+          e1[2] = c1[2] - o1[2];
+          e1[1] = c1[1] - fma(3.0 * dl, o1[2], o1[1]);
+          e1[0] = c1[0] - fma(1.5, o1[2], fma(dl, o1[1], o1[0]));
+          e2[2] = c2[2] - o2[2];
+          e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
+          e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
+          // physical scalings: normal derivative series (order 1, 2), tangential
+          // derivative of the value and of the normal derivative, second
+          // tangential derivative (a constant on the half-face)
+          const double a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
+          const double b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
+          const double t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
+          const double m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
+          const double tt = 3.0 * dt2 * e0[2];
+          const double tt2 = tt * tt;
+          double S0 = 0.0, S1 = 0.0, S2 = 0.0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        c0[a] = u[a] + s * u[3 + a] + u[6 + a];
-        c1[a] = fma(3.0 * s, u[6 + a], u[3 + a]);
-        c2[a] = 3.0 * u[6 + a];
-      }
-      const int oj = sy ? oj1 : oj0;
-#pragma unroll
-      for (int sx = 0; sx < 2; ++sx) {
-        const double* co = uo + f * 9 * P + (long long)oj * g.nx + (sx ? oi1 : oi0);
-        double o0[3], o1[3], o2[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double w0 = __ldg(co + a * P), w1 = __ldg(co + (3 + a) * P), w2 = __ldg(co + (6 + a) * P);
-          o0[a] = fma(-0.5, w2, w0);
-          o1[a] = w1;
-          o2[a] = 3.0 * w2;
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double es = xs_self(sx, q), eo = xs_other(sx, q);
-          const double D00 = (c0[0] + es * c0[1] + lp(2, es) * c0[2]) - (o0[0] + eo * o0[1] + lp(2, eo) * o0[2]);
-          const double D01 = (c1[0] + es * c1[1] + lp(2, es) * c1[2]) - (o1[0] + eo * o1[1] + lp(2, eo) * o1[2]);
-          const double D02 = (c2[0] + es * c2[1] + lp(2, es) * c2[2]) - (o2[0] + eo * o2[1] + lp(2, eo) * o2[2]);
-          const double D10 = (c0[1] + 3.0 * es * c0[2]) - (o0[1] + 3.0 * eo * o0[2]);
-          const double D11 = (c1[1] + 3.0 * es * c1[2]) - (o1[1] + 3.0 * eo * o1[2]);
-          const double D20 = 3.0 * (c0[2] - o0[2]);
-          const double e1x = dx1 * D10, e1y = dy1 * D01;
-          const double e2x = dx2 * D20, e2m = dxy * D11, e2y = dy2 * D02;
-          Sy0 = fma(gwt(q), fabs(D00), Sy0);
-          Sy1 = fma(gwt(q), sqrt(fma(e1x, e1x, e1y * e1y)), Sy1);
-          Sy2 = fma(gwt(q), sqrt(fma(e2x, e2x, fma(e2m, e2m, e2y * e2y))), Sy2);
+          for (int q = 0; q < 3; ++q) {
+            const double ts = xs_self(h, q);
+            const double p2 = lp(2, ts);
+            const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));   // u_K - w
+            const double gn = fma(p2, a2, fma(ts, a1, a0));           // normal derivative
+            const double gt = fma(ts, t1, t0);                        // tangential derivative
+            const double hn = fma(p2, b2, fma(ts, b1, b0));           // second normal
+            const double hm = fma(ts, m1, m0);                        // mixed
+            S0 = fma(gwt(q), fabs(v), S0);
+            S1 = fma(gwt(q), sqrt(fma(gn, gn, gt * gt)), S1);
+            S2 = fma(gwt(q), sqrt(fma(hn, hn, fma(hm, hm, tt2))), S2);
+          }
+          if (n == 0) {
+            Sx0 += S0;
+            Sx1 += S1;
+            Sx2 += S2;
+          } else {
+            Sy0 += S0;
+            Sy1 += S1;
+            Sy2 += S2;
+          }
         }
       }
     }
