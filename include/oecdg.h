@@ -200,6 +200,57 @@ cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const double* d_uh, do
 /* Number of kernels launched by the context so far (host-side counter). */
 cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
 
+/* ------------------------------------------------------------- batches ---
+ * Many independent 2D Euler Q^2 problems of uneven mesh sizes advanced together.
+ * Not in the paper: each instance is exactly the single-mesh scheme above
+ * (Eq. (eq:RKCDG) with SSP-RK3 and the OE step), with its own sigma, wave speed,
+ * tau and time.  Every phase of a step is one launch over the tiles of all
+ * instances (11 launches per step whatever the number of instances), and the
+ * launches of nsteps steps can be captured in a CUDA graph. */
+typedef struct cdg_batch cdg_batch;
+
+/* Create a batch of n instances (descs[q]: dim 2, k 2, basis Q, system Euler,
+ * rk SSP-RK3, oe 1; the same boundary condition for all), bound to `stream`
+ * (NULL: the batch creates and owns a non-blocking stream; graph capture needs
+ * a stream other than the legacy default).  Allocates per instance two scratch
+ * states and the reduction slots.  Errors: CDG_EINVAL, CDG_EUNSUPPORTED,
+ * CDG_ENOMEM, CDG_ECUDA. */
+cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_batch** out);
+
+/* Release a batch (synchronises its stream).  NULL is accepted. */
+cdg_status cdg_batch_free(cdg_batch* batch);
+
+/* Static text describing the batch's last error. */
+const char* cdg_batch_last_error(const cdg_batch* batch);
+
+/* nsteps SSP-RK3 steps of every instance, in place on the caller's device
+ * states d_us[0..n-1] (a host array of n device pointers, each with the
+ * single-mesh layout of its instance).  The instance table is re-uploaded
+ * (synchronously) only when the pointers change.  use_graph != 0: the launches
+ * of nsteps steps are captured once in a CUDA graph (re-captured when nsteps or
+ * the pointers change) and the graph is launched.  Asynchronous otherwise. */
+cdg_status cdg_batch_step(cdg_batch* batch, double* const* d_us, int nsteps, int use_graph);
+
+/* Read and clear the batch's status flag (synchronises): CDG_OK or
+ * CDG_ENONPHYSICAL. */
+cdg_status cdg_batch_check_status(cdg_batch* batch);
+
+/* Time of every instance (t[0..n-1], host); synchronises. */
+cdg_status cdg_batch_get_time(cdg_batch* batch, double* t);
+
+/* Kernels launched by the batch so far (graph launches count their kernels). */
+cdg_status cdg_batch_launch_count(const cdg_batch* batch, long long* count);
+
+/* Tile height (rows of 32 cells per block: 2, 4 or 8) currently in use. */
+cdg_status cdg_batch_rows(const cdg_batch* batch, int* rows);
+
+/* Pick the tile height for this batch: look it up in the JSON cache file
+ * `cache_path` (keyed by a signature of the mesh sizes; NULL: no cache), or
+ * time one stage + sigma + OE pass of each candidate (2, 4, 8 rows; it reads
+ * the states d_us and writes only scratch) and store the fastest.  Resets the
+ * instances' time to 0.  *rows_out (nullable) receives the choice. */
+cdg_status cdg_batch_autotune(cdg_batch* batch, double* const* d_us, const char* cache_path, int* rows_out);
+
 #ifdef __cplusplus
 }
 #endif

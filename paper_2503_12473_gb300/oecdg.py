@@ -29,6 +29,8 @@ EXPORTED = [
     "cdg_rhs", "cdg_compute_dt", "cdg_set_dt", "cdg_get_dt", "cdg_rk_stage", "cdg_oe_damp",
     "cdg_oe_coefficients", "cdg_step", "cdg_step_async", "cdg_get_time", "cdg_check_status", "cdg_launch_count",
     "cdg_profile_begin", "cdg_profile_end", "cdg_oe_damp_noalloc",
+    "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
+    "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
 ]
 
 
@@ -110,6 +112,24 @@ def load(build_if_missing: bool = True):
                                   ctypes.POINTER(ctypes.c_longlong)]
     L.cdg_oe_damp_noalloc.restype = st
     L.cdg_oe_damp_noalloc.argtypes = [ctypes.POINTER(cdg_mesh_desc), vp, ctypes.c_double, vp, vp]
+    L.cdg_init_batch.restype = st
+    L.cdg_init_batch.argtypes = [ctypes.POINTER(cdg_mesh_desc), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.cdg_batch_free.restype = st
+    L.cdg_batch_free.argtypes = [vp]
+    L.cdg_batch_last_error.restype = ctypes.c_char_p
+    L.cdg_batch_last_error.argtypes = [vp]
+    L.cdg_batch_step.restype = st
+    L.cdg_batch_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.cdg_batch_check_status.restype = st
+    L.cdg_batch_check_status.argtypes = [vp]
+    L.cdg_batch_get_time.restype = st
+    L.cdg_batch_get_time.argtypes = [vp, dp]
+    L.cdg_batch_launch_count.restype = st
+    L.cdg_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.cdg_batch_rows.restype = st
+    L.cdg_batch_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.cdg_batch_autotune.restype = st
+    L.cdg_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     L.cdg_launch_count.restype = st
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     _lib = L
@@ -306,3 +326,73 @@ class Context:
         u = self.zeros()
         self.cdg_project_ic(dv, u)
         return u
+
+
+class Batch:
+    """Owner of a cdg_batch (many independent 2D Euler Q^2 meshes stepped together)."""
+
+    def __init__(self, descs, stream=None):
+        L = load()
+        self._L = L
+        self.descs = list(descs)
+        self.n = len(self.descs)
+        arr = (cdg_mesh_desc * self.n)(*[d.c() for d in self.descs])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
+        s = L.cdg_init_batch(arr, self.n, sp, ctypes.byref(h))
+        if s != CDG_OK:
+            raise CdgError(s, "cdg_init_batch")
+        self.h = h
+
+    def _ck(self, s, what):
+        if s != CDG_OK:
+            msg = self._L.cdg_batch_last_error(self.h)
+            raise CdgError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def _ptrs(self, states):
+        if len(states) != self.n:
+            raise ValueError("one state per instance")
+        return (ctypes.c_void_p * self.n)(*[_ptr(u) for u in states])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._L.cdg_batch_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cdg_batch_step(self, states, nsteps: int = 1, use_graph: bool = False):
+        self._keep = self._ptrs(states)
+        self._ck(self._L.cdg_batch_step(self.h, self._keep, nsteps, int(bool(use_graph))), "cdg_batch_step")
+
+    def cdg_batch_check_status(self) -> int:
+        return self._L.cdg_batch_check_status(self.h)
+
+    def cdg_batch_get_time(self):
+        import numpy as np
+        t = np.zeros(self.n)
+        self._ck(self._L.cdg_batch_get_time(self.h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                 "cdg_batch_get_time")
+        return t
+
+    def cdg_batch_launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        self._ck(self._L.cdg_batch_launch_count(self.h, ctypes.byref(n)), "cdg_batch_launch_count")
+        return n.value
+
+    def cdg_batch_rows(self) -> int:
+        r = ctypes.c_int()
+        self._ck(self._L.cdg_batch_rows(self.h, ctypes.byref(r)), "cdg_batch_rows")
+        return r.value
+
+    def cdg_batch_autotune(self, states, cache_path=None) -> int:
+        self._keep = self._ptrs(states)
+        r = ctypes.c_int()
+        cp = cache_path.encode() if cache_path else None
+        self._ck(self._L.cdg_batch_autotune(self.h, self._keep, cp, ctypes.byref(r)), "cdg_batch_autotune")
+        return r.value
