@@ -119,6 +119,22 @@ def init_dist():
     return ws, rank, local
 
 
+def reduce_max_ms(ms: float, ws: int, device) -> float:
+    """Max over ranks of a duration (the slowest replica sets the job time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(dof: int, steps: int, ws: int, ms_max: float) -> float:
+    """Whole-job DOF-updates per second per RK stage: every rank advances its own
+    replica of `dof` degrees of freedom by `steps` three-stage steps."""
+    return 3.0 * dof * steps * ws / (ms_max * 1e-3)
+
+
 def config_dict(n, dof):
     return {"workload": f"euler_2d_riemann_q2_{n}", "model": None, "nx": n, "ny": n, "k": 2, "basis": "Q",
             "system": "euler", "bc": "transmissive", "rk": "ssp-rk3", "cfl": 0.1, "oe": True, "dof": dof,
@@ -225,11 +241,8 @@ def run_ours(args, ws, rank, local):
         if st != G.CDG_OK:
             raise G.CdgError(st, "timed steps")
         t_final = ctx.cdg_get_time()
-        ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms_max = ms_t.item()
-        value = 3.0 * dof * args.steps * ws / (ms_max * 1e-3)
+        ms_max = reduce_max_ms(ms, ws, "cuda")
+        value = job_value(dof, args.steps, ws, ms_max)
 
         # end to end through the C-ABI with host buffers: each step copies the
         # state from pinned host memory, steps, and copies the result back
@@ -248,10 +261,7 @@ def run_ours(args, ws, rank, local):
         e1.record(stream)
         barrier()
         e2e_ms = e0.elapsed_time(e1)
-        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e_value = 3.0 * dof * e2e_steps * ws / (e2e_t.item() * 1e-3)
+        e2e_value = job_value(dof, e2e_steps, ws, reduce_max_ms(e2e_ms, ws, "cuda"))
         state_bytes = dof * 8
 
     if ws > 1:
