@@ -373,6 +373,78 @@ def run_batched(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, ws, rank, local):
+    """Isentropic vortex (strength 5) on uniform flow (1, 1), [0,10]^2 periodic,
+    256^2 Q^2, plus a seeded 1e-3 Gaussian perturbation of every modal
+    coefficient; loss 0.5 ||rho(T) - rho_target||^2 over the rho modal
+    coefficients of both meshes, rho_target from the unperturbed run; gradient
+    w.r.t. the initial coefficients through all stages and OE steps with
+    sqrt(steps) checkpoints.  Reports adj/fwd = t(forward with checkpoints +
+    backward) / t(plain forward) and central finite differences on seeded
+    directions."""
+    import torch
+    from paper_2503_12473_gb300 import oecdg as G
+    from paper_2503_12473_gb300 import workloads as W
+    from paper_2503_12473_gb300.autograd import rollout
+
+    torch.cuda.set_device(local)
+    G.load()
+    n, nsteps = args.n if args.n != 1024 else 256, args.steps
+    w = W.vortex_2d(n=n)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w), stream=stream)
+    with torch.cuda.stream(stream):
+        base = ctx.project(w.u0)
+        target = base.clone()
+        ctx.cdg_step_async(target, 0.0, 0.0, nsteps)
+        target = target[:, 0].clone()
+        u0 = base + torch.from_numpy(W.perturbation(tuple(base.shape), args.seed + 1, 1e-3)).cuda()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        # plain forward
+        x = u0.clone()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        ctx.cdg_step_async(x, 0.0, 0.0, nsteps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_fwd = ev[0].elapsed_time(ev[1])
+        # forward with checkpoints + backward
+        ui = u0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        uT = rollout(ui, ctx, nsteps)
+        loss = 0.5 * ((uT[:, 0] - target) ** 2).sum()
+        loss.backward()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t_adj = ev[2].elapsed_time(ev[3])
+        grad = ui.grad.detach()
+
+        def L(v):
+            y = v.clone()
+            ctx.cdg_step_async(y, 0.0, 0.0, nsteps)
+            return 0.5 * ((y[:, 0] - target) ** 2).sum().item()
+
+        gen = torch.Generator(device="cpu").manual_seed(args.seed + 64)
+        fd = []
+        for _ in range(args.fd_dirs):
+            d = torch.randn(tuple(u0.shape), generator=gen, dtype=torch.float64).cuda()
+            an = (grad * d).sum().item()
+            row = {"analytic": an}
+            for h in (1e-6, 1e-8):
+                f = (L(u0 + h * d) - L(u0 - h * d)) / (2 * h)
+                row[f"rel_err_h{h:.0e}"] = abs(an - f) / max(abs(f), 1e-300)
+            fd.append(row)
+    line = {"metric": "adjoint cost adj/fwd, 2D Euler Q2 vortex", "workload": f"euler_2d_vortex_q2_{n}",
+            "steps": nsteps, "checkpoints": math.ceil(math.sqrt(nsteps)), "ms_forward": t_fwd,
+            "ms_forward_checkpointed_plus_backward": t_adj, "adj_over_fwd": t_adj / t_fwd,
+            "loss": loss.item(), "fd": fd,
+            "fd_max_rel_err_h1e-6": max(r["rel_err_h1e-06"] for r in fd) if fd else None,
+            "fd_max_rel_err_h1e-8": max(r["rel_err_h1e-08"] for r in fd) if fd else None,
+            "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,8 +454,10 @@ def main():
     ap.add_argument("--n", type=int, default=1024, help="cells per direction (the workload is 1024)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched"],
-                    help="riemann: the metric's workload (default); batched: 256 uneven meshes")
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched", "adjoint"],
+                    help="riemann: the metric's workload (default); batched: 256 uneven meshes; "
+                         "adjoint: gradient of the vortex loss (cost and finite-difference check)")
+    ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
@@ -394,6 +468,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batched":
         run_batched(args, ws, rank, local)
+    elif args.workload == "adjoint":
+        run_adjoint(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -150,6 +150,27 @@ cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int
 /* Device time after the last cdg_step / cdg_step_async; synchronises. */
 cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
 
+/* Adjoint of one time step (not in the paper; the forward step is Eq.
+ * (eq:RKCDG) with SSP-RK3 and the OE step after every stage):
+ *     d_lam = (d u^{n+1} / d u^n)^T d_lam_next,
+ * with tau = tau_max computed from u^n as in cdg_step (no end time).  The
+ * derivative follows every path the forward step takes: the CDG right-hand
+ * side (Euler flux Jacobians at the quadrature points, the dissipation term and
+ * 1/tau_max), the RK combination, the OE step (the exponential scaling, the
+ * damping coefficients through the half-face traces of u^C - u^D, the
+ * cell-average wave speeds beta, sigma through its extremal Gauss point and the
+ * domain average, and tau), and tau through the cell with the largest wave
+ * speed.  At non-differentiable points it takes sign(0) = 0, zero for the
+ * gradient of sqrt at a zero sum, and the lowest index for ties of max / argmax.
+ * The three stages are recomputed from d_un.  d_un, d_lam_next: device states
+ * (inputs); d_lam: device state (output, must not alias d_un; may alias
+ * d_lam_next); d_gtau: NULL or 2 device doubles receiving the adjoints of tau
+ * and tau_max of the step.  2D periodic SSP-RK3 only (CDG_EUNSUPPORTED
+ * otherwise); with oe = 0 the OE paths are left out as in the forward step.  The first call allocates the adjoint scratch
+ * (12 state-sized buffers) in the context.  Asynchronous. */
+cdg_status cdg_step_adjoint(cdg_ctx* ctx, const double* d_un, const double* d_lam_next, double* d_lam,
+                            double* d_gtau);
+
 /* Read and clear the device status flag (synchronises): CDG_OK or
  * CDG_ENONPHYSICAL. */
 cdg_status cdg_check_status(cdg_ctx* ctx);
@@ -240,6 +261,9 @@ cdg_status cdg_batch_get_time(cdg_batch* batch, double* t);
 
 /* Kernels launched by the batch so far (graph launches count their kernels). */
 cdg_status cdg_batch_launch_count(const cdg_batch* batch, long long* count);
+
+/* Set the tile height (2, 4 or 8 rows of 32 cells per block); synchronises. */
+cdg_status cdg_batch_set_rows(cdg_batch* batch, int rows);
 
 /* Tile height (rows of 32 cells per block: 2, 4 or 8) currently in use. */
 cdg_status cdg_batch_rows(const cdg_batch* batch, int* rows);

@@ -1,0 +1,56 @@
+"""torch.autograd.Function over n OECDG time steps with sqrt(n) checkpoints.
+
+Forward: cdg_step_async one step at a time, keeping the state every `segment`
+steps (segment = ceil(sqrt(n)) by default).  Backward: for each segment, last
+first, recompute its states from the checkpoint with cdg_step_async and run
+cdg_step_adjoint through them in reverse.  Peak memory: about 2 sqrt(n) states
+plus the library's adjoint scratch.  Every step and every adjoint runs in the
+CUDA library; this module only orders the calls.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+
+class OECDGRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, u0, context, nsteps: int, segment: int):
+        u = u0.detach().contiguous().clone()
+        chk = [u.clone()]
+        for s in range(nsteps):
+            context.cdg_step_async(u, 0.0, 0.0, 1)
+            if (s + 1) % segment == 0 and s + 1 < nsteps:
+                chk.append(u.clone())
+        fctx.context = context
+        fctx.nsteps = nsteps
+        fctx.segment = segment
+        fctx.chk = chk
+        return u
+
+    @staticmethod
+    def backward(fctx, lam_out):
+        ctx, n, seg = fctx.context, fctx.nsteps, fctx.segment
+        lam = lam_out.detach().contiguous().clone()
+        nxt = torch.empty_like(lam)
+        for k in reversed(range(len(fctx.chk))):
+            start = k * seg
+            end = min(start + seg, n)
+            states = [fctx.chk[k]]
+            for _ in range(start, end - 1):
+                u = states[-1].clone()
+                ctx.cdg_step_async(u, 0.0, 0.0, 1)
+                states.append(u)
+            for q in reversed(range(end - start)):
+                ctx.cdg_step_adjoint(states[q], lam, nxt)
+                lam, nxt = nxt, lam
+            del states
+        fctx.chk = None
+        return lam, None, None, None
+
+
+def rollout(u0: torch.Tensor, context, nsteps: int, segment: int | None = None) -> torch.Tensor:
+    """u(T) after nsteps steps, differentiable w.r.t. u0 (sqrt(n) checkpoints)."""
+    seg = segment or max(1, math.ceil(math.sqrt(nsteps)))
+    return OECDGRollout.apply(u0, context, nsteps, seg)

@@ -10,36 +10,10 @@
 
 #include "../../include/oecdg.h"
 #include "oecdg_common.cuh"
+#include "oecdg_ctx.h"
 #include "oecdg_kernels.h"
 
 using namespace oecdg;
-
-struct cdg_ctx {
-  cdg_mesh_desc d;
-  Geo g;
-  cudaStream_t stream;
-  int F, M;
-  size_t numel;
-  long long nblk;        // stage-kernel blocks per mesh (sigma partials)
-  int wave_blk;          // blocks of the wave-speed reduction
-  double* buf_a;         // scratch state (u_h)
-  double* buf_b;         // scratch state (u_sigma)
-  double* partials;      // [2][nblk][F][3]
-  double* wave_partial;  // [wave_blk][2]
-  double* dt;            // [tau, tau_max]
-  double* rhs_dt;        // [0, tau_max] for cdg_rhs
-  double* time;          // [t, unused]
-  double* sigma;         // [2][F]
-  double* avg;           // [2][F]
-  int* status;           // status bits
-  long long launches;
-  // optional per-kernel timing (cdg_profile_begin / cdg_profile_end)
-  int prof_on;
-  int prof_cap;
-  int prof_n[2];
-  cudaEvent_t* prof_ev[2];  // [class][2 * cap]: start, stop
-  char err[256];
-};
 
 enum { PROF_STAGE = 0, PROF_OE = 1 };
 
@@ -163,6 +137,7 @@ cdg_status cdg_free(cdg_ctx* c) {
   cudaFree(c->avg);
   cudaFree(c->status);
   prof_release(c);
+  adj_release(c);
   free(c);
   return CDG_OK;
 }

@@ -447,6 +447,12 @@ cdg_status cdg_batch_launch_count(const cdg_batch* B, long long* count) {
   return CDG_OK;
 }
 
+cdg_status cdg_batch_set_rows(cdg_batch* B, int rows) {
+  if (!B || (rows != 2 && rows != 4 && rows != 8)) return CDG_EINVAL;
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess || batch_layout(B, rows) != cudaSuccess) return CDG_ECUDA;
+  return CDG_OK;
+}
+
 cdg_status cdg_batch_rows(const cdg_batch* B, int* rows) {
   if (!B || !rows) return CDG_EINVAL;
   *rows = B->rows;

@@ -1,0 +1,42 @@
+// oecdg_ctx.h -- the context behind the C-ABI handle cdg_ctx (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/oecdg.h"
+#include "oecdg_common.cuh"
+
+using oecdg::Geo;
+
+struct AdjScratch;
+
+struct cdg_ctx {
+  cdg_mesh_desc d;
+  Geo g;
+  cudaStream_t stream;
+  int F, M;
+  size_t numel;
+  long long nblk;        // stage-kernel blocks per mesh (sigma partials)
+  int wave_blk;          // blocks of the wave-speed reduction
+  double* buf_a;         // scratch state (u_h)
+  double* buf_b;         // scratch state (u_sigma)
+  double* partials;      // [2][nblk][F][3]
+  double* wave_partial;  // [wave_blk][2]
+  double* dt;            // [tau, tau_max]
+  double* rhs_dt;        // [0, tau_max] for cdg_rhs
+  double* time;          // [t, unused]
+  double* sigma;         // [2][F]
+  double* avg;           // [2][F]
+  int* status;           // status bits
+  long long launches;
+  // optional per-kernel timing (cdg_profile_begin / cdg_profile_end)
+  int prof_on;
+  int prof_cap;
+  int prof_n[2];
+  cudaEvent_t* prof_ev[2];  // [class][2 * cap]: start, stop
+  struct AdjScratch* adj;   // adjoint buffers, allocated by the first cdg_step_adjoint
+  char err[256];
+};
+
+
+// release the adjoint scratch of a context (oecdg_adjoint.cu)
+void adj_release(cdg_ctx* c);

@@ -31,6 +31,7 @@ EXPORTED = [
     "cdg_profile_begin", "cdg_profile_end", "cdg_oe_damp_noalloc",
     "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
+    "cdg_step_adjoint", "cdg_batch_set_rows",
 ]
 
 
@@ -126,12 +127,16 @@ def load(build_if_missing: bool = True):
     L.cdg_batch_get_time.argtypes = [vp, dp]
     L.cdg_batch_launch_count.restype = st
     L.cdg_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.cdg_batch_set_rows.restype = st
+    L.cdg_batch_set_rows.argtypes = [vp, ctypes.c_int]
     L.cdg_batch_rows.restype = st
     L.cdg_batch_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.cdg_batch_autotune.restype = st
     L.cdg_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
     L.cdg_launch_count.restype = st
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.cdg_step_adjoint.restype = st
+    L.cdg_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -285,6 +290,10 @@ class Context:
     def cdg_step_async(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
         self._ck(self._L.cdg_step_async(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_async")
 
+    def cdg_step_adjoint(self, d_un, d_lam_next, d_lam, d_gtau=None):
+        self._ck(self._L.cdg_step_adjoint(self.h, _ptr(d_un), _ptr(d_lam_next), _ptr(d_lam), _ptr(d_gtau)),
+                 "cdg_step_adjoint")
+
     def cdg_get_time(self) -> float:
         t = ctypes.c_double()
         self._ck(self._L.cdg_get_time(self.h, ctypes.byref(t)), "cdg_get_time")
@@ -329,7 +338,10 @@ class Context:
 
 
 class Batch:
-    """Owner of a cdg_batch (many independent 2D Euler Q^2 meshes stepped together)."""
+    """Owner of a cdg_batch (many independent 2D Euler Q^2 meshes stepped together).
+
+    Without a stream the library creates its own non-blocking stream: results
+    are ready after cdg_batch_check_status() (or torch.cuda.synchronize())."""
 
     def __init__(self, descs, stream=None):
         L = load()
@@ -384,6 +396,9 @@ class Batch:
         n = ctypes.c_longlong()
         self._ck(self._L.cdg_batch_launch_count(self.h, ctypes.byref(n)), "cdg_batch_launch_count")
         return n.value
+
+    def cdg_batch_set_rows(self, rows: int):
+        self._ck(self._L.cdg_batch_set_rows(self.h, rows), "cdg_batch_set_rows")
 
     def cdg_batch_rows(self) -> int:
         r = ctypes.c_int()
