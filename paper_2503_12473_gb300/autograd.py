@@ -2,9 +2,10 @@
 
 Forward: cdg_step_async one step at a time, keeping the state every `segment`
 steps (segment = ceil(sqrt(n)) by default).  Backward: for each segment, last
-first, recompute its states from the checkpoint with cdg_step_async and run
-cdg_step_adjoint through them in reverse.  Peak memory: about 2 sqrt(n) states
-plus the library's adjoint scratch.  Every step and every adjoint runs in the
+first, recompute its steps from the checkpoint with cdg_step_record (which
+keeps each step's stages) and run cdg_step_adjoint_recorded through them in
+reverse.  Peak memory: sqrt(n) checkpoints plus 6 sqrt(n) states of records
+plus the library's adjoint scratch; every step is computed twice in all.  Every step and every adjoint runs in the
 CUDA library; this module only orders the calls.
 """
 from __future__ import annotations
@@ -34,18 +35,20 @@ class OECDGRollout(torch.autograd.Function):
         ctx, n, seg = fctx.context, fctx.nsteps, fctx.segment
         lam = lam_out.detach().contiguous().clone()
         nxt = torch.empty_like(lam)
+        rec_numel = ctx.cdg_record_numel()
         for k in reversed(range(len(fctx.chk))):
             start = k * seg
             end = min(start + seg, n)
-            states = [fctx.chk[k]]
-            for _ in range(start, end - 1):
-                u = states[-1].clone()
-                ctx.cdg_step_async(u, 0.0, 0.0, 1)
-                states.append(u)
+            u = fctx.chk[k].clone()
+            recs = []
+            for _ in range(start, end):
+                r = torch.empty(rec_numel, dtype=torch.float64, device=u.device)
+                ctx.cdg_step_record(u, r)
+                recs.append(r)
             for q in reversed(range(end - start)):
-                ctx.cdg_step_adjoint(states[q], lam, nxt)
+                ctx.cdg_step_adjoint_recorded(recs[q], lam, nxt)
                 lam, nxt = nxt, lam
-            del states
+            del recs, u
         fctx.chk = None
         return lam, None, None, None
 

@@ -283,11 +283,13 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
   }
 }
 
-template <int SYS, int BC, bool WRITE_DELTA>
+// REC = 1 also records, per cell and order m, (delta^m, the field that gives
+// the max, that field's x- and y-face sums) for the adjoint: rec[cell][3][4].
+template <int SYS, int BC, bool WRITE_DELTA, int REC = 0>
 __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
-                                          int j) {
+                                          int j, double* __restrict__ rec = nullptr) {
   constexpr int F = Fields<SYS>::F;
   if (i >= g.nx || j >= g.ny) return;
   const long long P = g.plane;
@@ -323,6 +325,8 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
   const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;  // reference -> physical derivative
 
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;  // max over fields
+  int rf[3] = {-1, -1, -1};             // REC: field of the max, and its face sums
+  double rs[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
   for (int f = 0; f < F; ++f) {
     const double sg = __ldg(sigma + mesh * F + f);
@@ -421,9 +425,29 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     }
     if (sg != 0.0) {
       const double is = 1.0 / sg;
-      d0 = fmax(d0, (bx * cx0 * Sx0 + by * cy0 * Sy0) * is);
-      d1 = fmax(d1, (bx * cx1 * Sx1 + by * cy1 * Sy1) * is);
-      d2 = fmax(d2, (bx * cx2 * Sx2 + by * cy2 * Sy2) * is);
+      if (REC) {
+        const double v0 = (bx * cx0 * Sx0 + by * cy0 * Sy0) * is;
+        const double v1 = (bx * cx1 * Sx1 + by * cy1 * Sy1) * is;
+        const double v2 = (bx * cx2 * Sx2 + by * cy2 * Sy2) * is;
+        if (v0 > d0) { d0 = v0; rf[0] = f; rs[0][0] = Sx0; rs[0][1] = Sy0; }
+        if (v1 > d1) { d1 = v1; rf[1] = f; rs[1][0] = Sx1; rs[1][1] = Sy1; }
+        if (v2 > d2) { d2 = v2; rf[2] = f; rs[2][0] = Sx2; rs[2][1] = Sy2; }
+      } else {
+        d0 = fmax(d0, (bx * cx0 * Sx0 + by * cy0 * Sy0) * is);
+        d1 = fmax(d1, (bx * cx1 * Sx1 + by * cy1 * Sy1) * is);
+        d2 = fmax(d2, (bx * cx2 * Sx2 + by * cy2 * Sy2) * is);
+      }
+    }
+  }
+  if (REC) {
+    double* r = rec + ((long long)mesh * P + (long long)j * g.nx + i) * 12;
+    const double dd[3] = {d0, d1, d2};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      r[4 * m] = dd[m];
+      r[4 * m + 1] = (double)rf[m];
+      r[4 * m + 2] = rs[m][0];
+      r[4 * m + 3] = rs[m][1];
     }
   }
   if (WRITE_DELTA) {

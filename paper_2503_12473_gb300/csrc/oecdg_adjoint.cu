@@ -112,8 +112,11 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
   const long long self = (long long)mesh * F * 9 * P + (long long)jc * g.nx + ic;
   const int off = mesh == 0 ? -1 : 0;
 
-  // R_bar[f][b][a] = (2a+1)(2b+1)/16 * s * lam_h
-  double Rb[F][3][3];
+  // R_bar[f][b][a] = (2a+1)(2b+1)/16 * s * lam_h, read through the cache where
+  // needed (keeps 36 doubles out of the registers)
+  const double sact = active ? s : 0.0;
+  const double* lself = lamh + self;
+#define RB(f, b, a) ((2 * (a) + 1) * (2 * (b) + 1) / 16.0 * sact * __ldg(lself + ((f) * 9 + (b) * 3 + (a)) * P))
   double tm_acc = 0.0, t_acc = 0.0;
 #pragma unroll
   for (int f = 0; f < F; ++f)
@@ -123,7 +126,6 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
       for (int a = 0; a < 3; ++a) {
         const long long id = self + (f * 9 + b * 3 + a) * P;
         const double lh = active ? __ldg(lamh + id) : 0.0;
-        Rb[f][b][a] = (2 * a + 1) * (2 * b + 1) / 16.0 * s * lh;
         const double uself = __ldg(uin + id);
         // own-cell term: -u/tau_max and its tau_max derivative
         tm_acc += s * lh * uself * inv_tm * inv_tm;
@@ -134,29 +136,30 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
       }
 
   const int oj0 = wrap_index<BC_PERIODIC>(jc + off, g.ny), oj1 = wrap_index<BC_PERIODIC>(jc + 1 + off, g.ny);
-#pragma unroll
-  for (int sx = 0; sx < 2; ++sx) {
+  // the four sub-cells one after the other (not unrolled: keeps the live
+  // registers of one sub-cell only)
+#pragma unroll 1
+  for (int s4 = 0; s4 < 4; ++s4) {
+    const int sx = s4 & 1, sy = s4 >> 1;
     const int oi = wrap_index<BC_PERIODIC>(ic + sx + off, g.nx);
-    double Wb[2][F][9];  // contributions to O(sx, 0), O(sx, 1)
-#pragma unroll
-    for (int sy = 0; sy < 2; ++sy)
-#pragma unroll
-      for (int f = 0; f < F; ++f)
-#pragma unroll
-        for (int m = 0; m < 9; ++m) Wb[sy][f][m] = 0.0;
-    // ---- x-face column (xi = 2 sx - 1): R += (-s P_a(s)) (4/hx) Bf
     {
-      double Bfb[F][3];
-      const double sc = 4.0 / g.hx;
+      // contributions to the overlapping cell O(sx, sy)
+      double Wb[F][9];
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-          Bfb[f][b] = sx ? -sc * (Rb[f][b][0] + Rb[f][b][1] + Rb[f][b][2])
-                         : sc * (Rb[f][b][0] - Rb[f][b][1] + Rb[f][b][2]);
+        for (int m = 0; m < 9; ++m) Wb[f][m] = 0.0;
+      const double* c = uo + (long long)(sy ? oj1 : oj0) * g.nx + oi;
+      // ---- x-face column (xi = 2 sx - 1): R += (-s P_a(s)) (4/hx) Bf
+      {
+        double Bfb[F][3];
+        const double sc = 4.0 / g.hx;
 #pragma unroll
-      for (int sy = 0; sy < 2; ++sy) {
-        const double* c = uo + (long long)(sy ? oj1 : oj0) * g.nx + oi;
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            Bfb[f][b] = sx ? -sc * (RB(f, b, 0) + RB(f, b, 1) + RB(f, b, 2))
+                           : sc * (RB(f, b, 0) - RB(f, b, 1) + RB(f, b, 2));
         double T[F][3], Tb[F][3];
 #pragma unroll
         for (int f = 0; f < F; ++f)
@@ -189,27 +192,24 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
         for (int f = 0; f < F; ++f)
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
-            Wb[sy][f][b * 3] += Tb[f][b];
-            Wb[sy][f][b * 3 + 2] -= 0.5 * Tb[f][b];
+            Wb[f][b * 3] += Tb[f][b];
+            Wb[f][b * 3 + 2] -= 0.5 * Tb[f][b];
           }
       }
-    }
-    // ---- volume columns
+      // ---- the three volume columns of this half, points of sub-cell (sx, sy)
 #pragma unroll
-    for (int qx = 0; qx < 3; ++qx) {
-      const double xo = xs_other(sx, qx), xsf = xs_self(sx, qx);
-      const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
-      double Ab[F][3], Bb[F][3];
+      for (int qx = 0; qx < 3; ++qx) {
+        const double xo = xs_other(sx, qx), xsf = xs_self(sx, qx);
+        const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
+        double Ab[F][3], Bb[F][3];
 #pragma unroll
-      for (int f = 0; f < F; ++f)
+        for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          Ab[f][b] = wa * (Rb[f][b][0] + xsf * Rb[f][b][1] + lp(2, xsf) * Rb[f][b][2]);
-          Bb[f][b] = wb * (Rb[f][b][1] + dlp(2, xsf) * Rb[f][b][2]);
-        }
-#pragma unroll
-      for (int sy = 0; sy < 2; ++sy) {
-        const double* c = uo + (long long)(sy ? oj1 : oj0) * g.nx + oi;
+          for (int b = 0; b < 3; ++b) {
+            const double r0 = RB(f, b, 0), r1 = RB(f, b, 1), r2 = RB(f, b, 2);
+            Ab[f][b] = wa * (r0 + xsf * r1 + lp(2, xsf) * r2);
+            Bb[f][b] = wb * (r1 + dlp(2, xsf) * r2);
+          }
         double T[F][3], Tb[F][3];
 #pragma unroll
         for (int f = 0; f < F; ++f)
@@ -263,23 +263,21 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
         for (int f = 0; f < F; ++f)
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
-            Wb[sy][f][b * 3] += Tb[f][b];
-            Wb[sy][f][b * 3 + 1] += xo * Tb[f][b];
-            Wb[sy][f][b * 3 + 2] += lp(2, xo) * Tb[f][b];
+            Wb[f][b * 3] += Tb[f][b];
+            Wb[f][b * 3 + 1] += xo * Tb[f][b];
+            Wb[f][b * 3 + 2] += lp(2, xo) * Tb[f][b];
           }
       }
-    }
-    if (active) {
-#pragma unroll
-      for (int sy = 0; sy < 2; ++sy) {
+      if (active) {
         double* sl = slots + slot_off(numel, sx + 2 * sy) + self;
 #pragma unroll
         for (int f = 0; f < F; ++f)
 #pragma unroll
-          for (int m = 0; m < 9; ++m) sl[(f * 9 + m) * P] = Wb[sy][f][m];
+          for (int m = 0; m < 9; ++m) sl[(f * 9 + m) * P] = Wb[f][m];
       }
     }
   }
+#undef RB
   if (!active) {
     tm_acc = 0.0;
     t_acc = 0.0;
@@ -622,35 +620,51 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
         const double tt = 3.0 * dt2 * e0[2];
         double e0b[3] = {0, 0, 0}, a0b = 0, a1b = 0, a2b = 0, b0b = 0, b1b = 0, b2b = 0;
         double t0b = 0, t1b = 0, m0b = 0, m1b = 0, ttb = 0;
+        // only the derivative orders whose adjoint is non-zero (the field
+        // gives the max of delta^m for those m only)
+        if (Sb[n][0] != 0.0) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double ts = xs_self(h, q), p2 = lp(2, ts);
-          const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));
-          const double gn = fma(p2, a2, fma(ts, a1, a0));
-          const double gt = fma(ts, t1, t0);
-          const double hn = fma(p2, b2, fma(ts, b1, b0));
-          const double hm = fma(ts, m1, m0);
-          const double w = gwt(q);
-          const double vb = w * Sb[n][0] * (v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0));
-          const double r1 = sqrt(fma(gn, gn, gt * gt));
-          const double k1 = r1 > 0.0 ? w * Sb[n][1] / r1 : 0.0;
-          const double r2 = sqrt(fma(hn, hn, fma(hm, hm, tt * tt)));
-          const double k2 = r2 > 0.0 ? w * Sb[n][2] / r2 : 0.0;
-          const double gnb = k1 * gn, gtb = k1 * gt, hnb = k2 * hn, hmb = k2 * hm;
-          ttb += k2 * tt;
-          e0b[0] += vb;
-          e0b[1] += ts * vb;
-          e0b[2] += p2 * vb;
-          a0b += gnb;
-          a1b += ts * gnb;
-          a2b += p2 * gnb;
-          t0b += gtb;
-          t1b += ts * gtb;
-          b0b += hnb;
-          b1b += ts * hnb;
-          b2b += p2 * hnb;
-          m0b += hmb;
-          m1b += ts * hmb;
+          for (int q = 0; q < 3; ++q) {
+            const double ts = xs_self(h, q), p2 = lp(2, ts);
+            const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));
+            const double vb = gwt(q) * Sb[n][0] * (v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0));
+            e0b[0] += vb;
+            e0b[1] += ts * vb;
+            e0b[2] += p2 * vb;
+          }
+        }
+        if (Sb[n][1] != 0.0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const double ts = xs_self(h, q), p2 = lp(2, ts);
+            const double gn = fma(p2, a2, fma(ts, a1, a0));
+            const double gt = fma(ts, t1, t0);
+            const double r1 = sqrt(fma(gn, gn, gt * gt));
+            const double k1 = r1 > 0.0 ? gwt(q) * Sb[n][1] / r1 : 0.0;
+            const double gnb = k1 * gn, gtb = k1 * gt;
+            a0b += gnb;
+            a1b += ts * gnb;
+            a2b += p2 * gnb;
+            t0b += gtb;
+            t1b += ts * gtb;
+          }
+        }
+        if (Sb[n][2] != 0.0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const double ts = xs_self(h, q), p2 = lp(2, ts);
+            const double hn = fma(p2, b2, fma(ts, b1, b0));
+            const double hm = fma(ts, m1, m0);
+            const double r2 = sqrt(fma(hn, hn, fma(hm, hm, tt * tt)));
+            const double k2 = r2 > 0.0 ? gwt(q) * Sb[n][2] / r2 : 0.0;
+            const double hnb = k2 * hn, hmb = k2 * hm;
+            ttb += k2 * tt;
+            b0b += hnb;
+            b1b += ts * hnb;
+            b2b += p2 * hnb;
+            m0b += hmb;
+            m1b += ts * hmb;
+          }
         }
         // back through the scalings
         e0b[1] += dt1 * t0b;
@@ -695,14 +709,27 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
   }
 }
 
-// Adjoint of the OE step of one cell: lam_h[K] (own modes) and the slots of
-// the 4 overlapping cells; block partials of tau_bar and sigma_bar[f].
-// stats: (avg, max, argmax, min, argmin, sigma) per mesh and field.
+// Forward OE step that also records (delta^m, field of the max, its face
+// sums) per cell for the adjoint.
+template <int SYS>
+__global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
+                                                 const double* __restrict__ dt, const double* __restrict__ sigma,
+                                                 int* __restrict__ status, double* __restrict__ rec) {
+  oe_cell2d<SYS, BC_PERIODIC, false, 1>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
+                                         blockIdx.x * 32 + (threadIdx.x & 31),
+                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec);
+}
+
+// Adjoint of the OE step of one cell from its record: lam_h[K] (own modes)
+// and the slots of the 4 overlapping cells; block partials of tau_bar and
+// sigma_bar[f].  stats: (avg, max, argmax, min, argmin, sigma) per mesh and
+// field.
 template <int SYS>
 __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict__ uh, const double* __restrict__ lams,
                                                  double* __restrict__ lamh, double* __restrict__ slots,
                                                  const double* __restrict__ dt, const double* __restrict__ stats,
-                                                 double* __restrict__ part_t, double* __restrict__ part_sig) {
+                                                 const double* __restrict__ rec, double* __restrict__ part_t,
+                                                 double* __restrict__ part_sig) {
   constexpr int F = Fields<SYS>::F;
   __shared__ double sh[32];
   const int mesh = blockIdx.z;
@@ -730,28 +757,16 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
   const double cx[3] = {1.0 / (12.0 * g.hx), 0.25, 5.0 * g.hx / 24.0};
   const double cy[3] = {1.0 / (12.0 * g.hy), 0.25, 5.0 * g.hy / 24.0};
 
-  // forward: per-field delta^m(f), then the max over fields
-  double Sx[F][3], Sy[F][3], dl[F][3];
-  double d[3] = {0.0, 0.0, 0.0};
-  int arg[3] = {-1, -1, -1};
+  // the forward's delta^m, the field of the max and its face sums
+  const double* r = rec + ((long long)mesh * P + (long long)jc * g.nx + ic) * 12;
+  double d[3], Sxm[3], Sym[3];
+  int arg[3];
 #pragma unroll
-  for (int f = 0; f < F; ++f) {
-    double u[9];
-#pragma unroll
-    for (int m = 0; m < 9; ++m) u[m] = uh[self + (f * 9 + m) * P];
-    double S[2][3];
-    oe_face_sums(g, u, uo + f * 9 * P, oi, oj, S);
-    const double sg = stats[(mesh * F + f) * 6 + 5];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      Sx[f][m] = S[0][m];
-      Sy[f][m] = S[1][m];
-      dl[f][m] = sg != 0.0 ? (bx * cx[m] * S[0][m] + by * cy[m] * S[1][m]) / sg : 0.0;
-      if (dl[f][m] > d[m]) {
-        d[m] = dl[f][m];
-        arg[m] = f;
-      }
-    }
+  for (int m = 0; m < 3; ++m) {
+    d[m] = r[4 * m];
+    arg[m] = (int)r[4 * m + 1];
+    Sxm[m] = r[4 * m + 2];
+    Sym[m] = r[4 * m + 3];
   }
   const double r1 = d[0] + d[1], r2 = r1 + d[2];
   const double e1 = exp(-tau * r1), e2 = exp(-tau * r2);
@@ -775,14 +790,7 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
   // delta^m = delta^m(arg[m]) = (bx cx Sx + by cy Sy) / sigma
   double bxb = 0.0, byb = 0.0;
   double sigb[F];
-  double slot_acc[4][F][9];
-#pragma unroll
-  for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-    for (int f = 0; f < F; ++f)
-#pragma unroll
-      for (int m = 0; m < 9; ++m) slot_acc[s4][f][m] = 0.0;
-#pragma unroll
+#pragma unroll 1
   for (int f = 0; f < F; ++f) {
     sigb[f] = 0.0;
     double Sb[2][3];
@@ -795,12 +803,17 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
         const double k = db[m] / sg;
         Sb[0][m] = k * bx * cx[m];
         Sb[1][m] = k * by * cy[m];
-        bxb += k * cx[m] * Sx[f][m];
-        byb += k * cy[m] * Sy[f][m];
-        sigb[f] -= db[m] * dl[f][m] / sg;
+        bxb += k * cx[m] * Sxm[m];
+        byb += k * cy[m] * Sym[m];
+        sigb[f] -= db[m] * d[m] / sg;
         any = true;
       }
     }
+    double wbl[4][9];
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+      for (int m = 0; m < 9; ++m) wbl[s4][m] = 0.0;
     if (any) {
       double u[9], ub[9];
 #pragma unroll
@@ -808,34 +821,23 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
         u[m] = uh[self + (f * 9 + m) * P];
         ub[m] = 0.0;
       }
-      double wbl[4][9];
-#pragma unroll
-      for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-        for (int m = 0; m < 9; ++m) wbl[s4][m] = 0.0;
       oe_face_sums_vjp(g, u, uo + f * 9 * P, oi, oj, Sb, ub, wbl);
 #pragma unroll
       for (int m = 0; m < 9; ++m) lamh[self + (f * 9 + m) * P] += ub[m];
+    }
+    if (active) {
 #pragma unroll
-      for (int s4 = 0; s4 < 4; ++s4)
+      for (int s4 = 0; s4 < 4; ++s4) {
+        double* sl = slots + slot_off(numel, s4) + self + (long long)f * 9 * P;
 #pragma unroll
-        for (int m = 0; m < 9; ++m) slot_acc[s4][f][m] = wbl[s4][m];
+        for (int m = 0; m < 9; ++m) sl[m * P] = wbl[s4][m];
+      }
     }
   }
   // beta at the cell average (mode 0)
   if (active && SYS == SYS_EULER) {
 #pragma unroll
     for (int f = 0; f < F; ++f) lamh[self + f * 9 * P] += bxb * gbx[f] + byb * gby[f];
-  }
-  if (active) {
-#pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-      double* sl = slots + slot_off(numel, s4) + self;
-#pragma unroll
-      for (int f = 0; f < F; ++f)
-#pragma unroll
-        for (int m = 0; m < 9; ++m) sl[(f * 9 + m) * P] = slot_acc[s4][f][m];
-    }
   }
   if (!active) t_acc = 0.0;
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -1015,6 +1017,7 @@ struct AdjScratch {
   double* scal;     // [tau_bar, tau_max_bar]
   double* wpart;    // [WBLK 4]
   double* time;     // scratch time slot of the recompute
+  double* rec[3];   // OE records of the three stages: [2 plane][12]
   long long nb, nb256;
 };
 
@@ -1043,7 +1046,7 @@ static cdg_status adj_alloc(cdg_ctx* c) {
   a->nb256 = (g.plane + 255) / 256;
   const size_t n = c->numel;
   size_t tot = 12 * n + 2 * a->nb * 2 + (size_t)2 * F * a->nb + (size_t)2 * a->nb256 * F * 5 + 2 * F * 6 + 2 * F + 2 +
-               ADJ_WBLK * 4 + 2;
+               ADJ_WBLK * 4 + 2 + 3 * (size_t)24 * g.plane;
   double* p = nullptr;
   if (cudaMalloc((void**)&p, tot * sizeof(double)) != cudaSuccess) {
     free(a);
@@ -1067,12 +1070,16 @@ static cdg_status adj_alloc(cdg_ctx* c) {
   a->scal = p; p += 2;
   a->wpart = p; p += ADJ_WBLK * 4;
   a->time = p; p += 2;
+  for (int l = 0; l < 3; ++l) {
+    a->rec[l] = p;
+    p += (size_t)24 * g.plane;
+  }
   c->adj = a;
   return CDG_OK;
 }
 
 template <int SYS>
-static cudaError_t adj_oe(cdg_ctx* c, const double* uh, const double* lams, double* lamh) {
+static cudaError_t adj_oe(cdg_ctx* c, const double* uh, const double* lams, double* lamh, const double* rec) {
   constexpr int F = Fields<SYS>::F;
   AdjScratch* a = c->adj;
   const Geo& g = c->g;
@@ -1080,7 +1087,7 @@ static cudaError_t adj_oe(cdg_ctx* c, const double* uh, const double* lams, doub
   const dim3 grid((g.nx + 31) / 32, (g.ny + AT / 32 - 1) / (AT / 32), 2);
   k_sigma_stats2d<F><<<dim3((unsigned)a->nb256, 2), 256, 0, st>>>(g, uh, a->sstat_part);
   k_sigma_stats_final<<<dim3(F, 2), 32, 0, st>>>(a->sstat_part, a->nb256, F, g.plane, a->stats);
-  k_oe_vjp2d<SYS><<<grid, AT, 0, st>>>(g, uh, lams, lamh, a->slots, c->dt, a->stats, a->part_t, a->part_sig);
+  k_oe_vjp2d<SYS><<<grid, AT, 0, st>>>(g, uh, lams, lamh, a->slots, c->dt, a->stats, rec, a->part_t, a->part_sig);
   k_acc_partials<<<1, 1024, 0, st>>>(a->part_t, 2 * a->nb, a->scal);
   k_zero<<<1, 32, 0, st>>>(a->sigb, 2 * F);
   for (int q = 0; q < 2 * F; ++q) k_acc_partials<<<1, 1024, 0, st>>>(a->part_sig + q * a->nb, a->nb, a->sigb + q);
@@ -1107,52 +1114,72 @@ static cudaError_t adj_stage(cdg_ctx* c, const double* uin, const double* un, co
   return cudaGetLastError();
 }
 
+// Forward step that records what the adjoint needs: u_h of the three stages
+// (H[0..2]) and u_sigma of the first two (S[0..1]); u is advanced in place
+// when u_next != nullptr (S[2] := u^{n+1}).  tau, tau_max land in dt.
 template <int SYS>
-static cudaError_t adj_step(cdg_ctx* c, const double* un, const double* lam_next, double* lam, double* gtau) {
+static cudaError_t adj_forward(cdg_ctx* c, const double* un, double* const* H, double* const* S, double* u_next,
+                               double* dt, double* const* R) {
   constexpr int F = Fields<SYS>::F;
   AdjScratch* a = c->adj;
   const Geo& g = c->g;
   cudaStream_t st = c->stream;
   const int sys = SYS;
-  const long long n = (long long)c->numel;
+  const bool oe = c->d.oe != 0;
   cudaError_t e;
-  // ---- forward recompute of the three stages
   if ((e = launch_set2(a->time, 0.0, 0.0, st)) != cudaSuccess) return e;
-  if ((e = launch_dt2d(sys, g, un, c->wave_partial, c->wave_blk, 0.0, c->dt, a->time, c->status, st)) != cudaSuccess)
+  if ((e = launch_dt2d(sys, g, un, c->wave_partial, c->wave_blk, 0.0, dt, a->time, c->status, st)) != cudaSuccess)
     return e;
   const double C[3] = {0.0, 0.75, 1.0 / 3.0};
-  const bool oe = c->d.oe != 0;
-  // stage inputs: u^n, then the OE output of the previous stage (without OE: its u_h)
-  const double* uin[3] = {un, oe ? a->S[0] : a->H[0], oe ? a->S[1] : a->H[1]};
+  const double* uin[3] = {un, oe ? S[0] : H[0], oe ? S[1] : H[1]};
   for (int l = 0; l < 3; ++l) {
-    if ((e = launch_stage2d(sys, BC_PERIODIC, g, 0, uin[l], un, a->H[l], c->dt, C[l], 1.0 - C[l], c->partials, st)) !=
+    if ((e = launch_stage2d(sys, BC_PERIODIC, g, 0, uin[l], un, H[l], dt, C[l], 1.0 - C[l], c->partials, st)) !=
         cudaSuccess)
       return e;
-    if (l < 2 && oe) {
+    // the last stage's OE output is u^{n+1}; without u_next it is still run
+    // (into the stage buffer H[2]'s partner slot) for its record
+    double* dst = l < 2 ? S[l] : (u_next ? u_next : a->LI);
+    if (oe) {
       if ((e = launch_sigma(c->partials, c->nblk, F, g.plane, c->sigma, c->avg, st)) != cudaSuccess) return e;
-      if ((e = launch_oe2d(sys, BC_PERIODIC, g, a->H[l], a->S[l], c->dt, c->sigma, nullptr, c->status, st)) !=
-          cudaSuccess)
-        return e;
+      const dim3 grid((g.nx + 31) / 32, (g.ny + AT / 32 - 1) / (AT / 32), 2);
+      k_oe_rec2d<SYS><<<grid, AT, 0, st>>>(g, H[l], dst, dt, c->sigma, c->status, R[l]);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if ((e = cudaMemcpyAsync(dst, H[l], c->numel * sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
+               cudaSuccess) {
+      return e;
     }
   }
-  c->launches += 3 + 3 + 2 * 2;
-  // ---- backward
+  c->launches += 3 + 3 + 2 * 3;
+  return cudaSuccess;
+}
+
+// Backward through one recorded step: lam = (du^{n+1}/du^n)^T lam_next.
+template <int SYS>
+static cudaError_t adj_backward(cdg_ctx* c, const double* un, const double* const* H, const double* const* S,
+                                const double* const* R, const double* lam_next, double* lam, double* gtau) {
+  AdjScratch* a = c->adj;
+  const Geo& g = c->g;
+  cudaStream_t st = c->stream;
+  const long long n = (long long)c->numel;
+  const bool oe = c->d.oe != 0;
+  const double C[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double* uin[3] = {un, oe ? S[0] : H[0], oe ? S[1] : H[1]};
+  cudaError_t e;
   k_zero<<<1, 32, 0, st>>>(a->scal, 2);
   const double* lam_s = lam_next;
   for (int l = 2; l >= 0; --l) {
     if (oe) {
-      if ((e = adj_oe<SYS>(c, a->H[l], lam_s, a->LH)) != cudaSuccess) return e;
+      if ((e = adj_oe<SYS>(c, H[l], lam_s, a->LH, R[l])) != cudaSuccess) return e;
     } else {
       k_axpby<<<1184, 256, 0, st>>>(n, lam_s, 1.0, a->LH, 0.0);
     }
-    if ((e = adj_stage<SYS>(c, uin[l], un, a->H[l], a->LH, a->LI, C[l], 1.0 - C[l])) != cudaSuccess) return e;
+    if ((e = adj_stage<SYS>(c, uin[l], un, H[l], a->LH, a->LI, C[l], 1.0 - C[l])) != cudaSuccess) return e;
     // lambda^n += c_l lambda_h (+ lambda_in for the first stage, whose input is u^n)
-    const unsigned nbk = 1184;
-    if (l == 2) k_axpby<<<nbk, 256, 0, st>>>(n, a->LH, C[l], a->LN, 0.0);
-    else if (l == 1) k_axpby<<<nbk, 256, 0, st>>>(n, a->LH, C[l], a->LN, 1.0);
-    else k_axpby<<<nbk, 256, 0, st>>>(n, a->LI, 1.0, a->LN, 1.0);
+    if (l == 2) k_axpby<<<1184, 256, 0, st>>>(n, a->LH, C[l], a->LN, 0.0);
+    else if (l == 1) k_axpby<<<1184, 256, 0, st>>>(n, a->LH, C[l], a->LN, 1.0);
+    else k_axpby<<<1184, 256, 0, st>>>(n, a->LI, 1.0, a->LN, 1.0);
     lam_s = a->LI;
-    c->launches += 1;
+    c->launches += 2;
   }
   // ---- tau = tau_max through the largest wave speed of u^n
   k_wave_stats2d<SYS><<<ADJ_WBLK, 256, 0, st>>>(g, un, a->wpart);
@@ -1164,19 +1191,81 @@ static cudaError_t adj_step(cdg_ctx* c, const double* un, const double* lam_next
   return cudaGetLastError();
 }
 
+static cdg_status adj_check(cdg_ctx* ctx) {
+  if (ctx->d.dim != 2 || ctx->d.bc != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
+    return adj_fail(ctx, CDG_EUNSUPPORTED, "adjoint: 2D periodic SSP-RK3 only");
+  cdg_status s = adj_alloc(ctx);
+  if (s != CDG_OK) return adj_fail(ctx, s, "adjoint: allocation failed");
+  return CDG_OK;
+}
+
+static cdg_status adj_cuda(cdg_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return CDG_OK;
+  snprintf(ctx->err, sizeof ctx->err, "%s: %s", where, cudaGetErrorString(e));
+  return CDG_ECUDA;
+}
+
+// record layout: [u^n][H0][S0][H1][S1][H2][tau, tau_max][OE records of 3 stages: 3 x 2 plane x 12]
+static size_t rec_oe_numel(const cdg_ctx* ctx) { return (size_t)24 * ctx->g.plane; }
+
+extern "C" cdg_status cdg_record_numel(const cdg_ctx* ctx, size_t* numel) {
+  if (!ctx || !numel) return CDG_EINVAL;
+  *numel = 6 * ctx->numel + 2 + 3 * rec_oe_numel(ctx);
+  return CDG_OK;
+}
+
+extern "C" cdg_status cdg_step_record(cdg_ctx* ctx, double* d_u, double* d_rec) {
+  if (!ctx || !d_u || !d_rec) return adj_fail(ctx, CDG_EINVAL, "step_record: null pointer");
+  cdg_status s = adj_check(ctx);
+  if (s != CDG_OK) return s;
+  const size_t n = ctx->numel;
+  double* U = d_rec;
+  double* H[3] = {d_rec + n, d_rec + 3 * n, d_rec + 5 * n};
+  double* S[2] = {d_rec + 2 * n, d_rec + 4 * n};
+  double* dt = d_rec + 6 * n;
+  double* R[3] = {dt + 2, dt + 2 + rec_oe_numel(ctx), dt + 2 + 2 * rec_oe_numel(ctx)};
+  cudaError_t e = cudaMemcpyAsync(U, d_u, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = ctx->d.system == CDG_EULER ? adj_forward<SYS_EULER>(ctx, U, H, S, d_u, dt, R)
+                                   : adj_forward<SYS_ADV>(ctx, U, H, S, d_u, dt, R);
+  return adj_cuda(ctx, e, "step_record");
+}
+
+extern "C" cdg_status cdg_step_adjoint_recorded(cdg_ctx* ctx, const double* d_rec, const double* d_lam_next,
+                                                double* d_lam, double* d_gtau) {
+  if (!ctx || !d_rec || !d_lam_next || !d_lam) return adj_fail(ctx, CDG_EINVAL, "step_adjoint_recorded: null pointer");
+  cdg_status s = adj_check(ctx);
+  if (s != CDG_OK) return s;
+  const size_t n = ctx->numel;
+  const double* U = d_rec;
+  const double* H[3] = {d_rec + n, d_rec + 3 * n, d_rec + 5 * n};
+  const double* S[2] = {d_rec + 2 * n, d_rec + 4 * n};
+  const double* R0 = d_rec + 6 * n + 2;
+  const double* R[3] = {R0, R0 + rec_oe_numel(ctx), R0 + 2 * rec_oe_numel(ctx)};
+  cudaError_t e = cudaMemcpyAsync(ctx->dt, d_rec + 6 * n, 2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = ctx->d.system == CDG_EULER ? adj_backward<SYS_EULER>(ctx, U, H, S, R, d_lam_next, d_lam, d_gtau)
+                                   : adj_backward<SYS_ADV>(ctx, U, H, S, R, d_lam_next, d_lam, d_gtau);
+  return adj_cuda(ctx, e, "step_adjoint_recorded");
+}
+
 extern "C" cdg_status cdg_step_adjoint(cdg_ctx* ctx, const double* d_un, const double* d_lam_next, double* d_lam,
                                        double* d_gtau) {
   if (!ctx || !d_un || !d_lam_next || !d_lam) return adj_fail(ctx, CDG_EINVAL, "step_adjoint: null pointer");
-  if (ctx->d.dim != 2 || ctx->d.bc != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
-    return adj_fail(ctx, CDG_EUNSUPPORTED, "step_adjoint: 2D periodic SSP-RK3 only");
   if (d_lam == d_un) return adj_fail(ctx, CDG_EINVAL, "step_adjoint: d_lam aliases d_un");
-  cdg_status s = adj_alloc(ctx);
-  if (s != CDG_OK) return adj_fail(ctx, s, "step_adjoint: allocation failed");
-  cudaError_t e = ctx->d.system == CDG_EULER ? adj_step<SYS_EULER>(ctx, d_un, d_lam_next, d_lam, d_gtau)
-                                             : adj_step<SYS_ADV>(ctx, d_un, d_lam_next, d_lam, d_gtau);
-  if (e != cudaSuccess) {
-    snprintf(ctx->err, sizeof ctx->err, "step_adjoint: %s", cudaGetErrorString(e));
-    return CDG_ECUDA;
-  }
-  return CDG_OK;
+  cdg_status s = adj_check(ctx);
+  if (s != CDG_OK) return s;
+  AdjScratch* a = ctx->adj;
+  double* H[3] = {a->H[0], a->H[1], a->H[2]};
+  double* S[2] = {a->S[0], a->S[1]};
+  const double* Hc[3] = {a->H[0], a->H[1], a->H[2]};
+  const double* Sc[2] = {a->S[0], a->S[1]};
+  double* R[3] = {a->rec[0], a->rec[1], a->rec[2]};
+  const double* Rc[3] = {a->rec[0], a->rec[1], a->rec[2]};
+  cudaError_t e = ctx->d.system == CDG_EULER ? adj_forward<SYS_EULER>(ctx, d_un, H, S, nullptr, ctx->dt, R)
+                                             : adj_forward<SYS_ADV>(ctx, d_un, H, S, nullptr, ctx->dt, R);
+  if (e == cudaSuccess)
+    e = ctx->d.system == CDG_EULER ? adj_backward<SYS_EULER>(ctx, d_un, Hc, Sc, Rc, d_lam_next, d_lam, d_gtau)
+                                   : adj_backward<SYS_ADV>(ctx, d_un, Hc, Sc, Rc, d_lam_next, d_lam, d_gtau);
+  return adj_cuda(ctx, e, "step_adjoint");
 }

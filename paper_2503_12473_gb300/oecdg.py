@@ -31,7 +31,7 @@ EXPORTED = [
     "cdg_profile_begin", "cdg_profile_end", "cdg_oe_damp_noalloc",
     "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
-    "cdg_step_adjoint", "cdg_batch_set_rows",
+    "cdg_step_adjoint", "cdg_batch_set_rows", "cdg_record_numel", "cdg_step_record", "cdg_step_adjoint_recorded",
 ]
 
 
@@ -137,6 +137,12 @@ def load(build_if_missing: bool = True):
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.cdg_step_adjoint.restype = st
     L.cdg_step_adjoint.argtypes = [vp, vp, vp, vp, vp]
+    L.cdg_record_numel.restype = st
+    L.cdg_record_numel.argtypes = [vp, ctypes.POINTER(sz)]
+    L.cdg_step_record.restype = st
+    L.cdg_step_record.argtypes = [vp, vp, vp]
+    L.cdg_step_adjoint_recorded.restype = st
+    L.cdg_step_adjoint_recorded.argtypes = [vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -293,6 +299,18 @@ class Context:
     def cdg_step_adjoint(self, d_un, d_lam_next, d_lam, d_gtau=None):
         self._ck(self._L.cdg_step_adjoint(self.h, _ptr(d_un), _ptr(d_lam_next), _ptr(d_lam), _ptr(d_gtau)),
                  "cdg_step_adjoint")
+
+    def cdg_record_numel(self) -> int:
+        n = ctypes.c_size_t()
+        self._ck(self._L.cdg_record_numel(self.h, ctypes.byref(n)), "cdg_record_numel")
+        return n.value
+
+    def cdg_step_record(self, d_u, d_rec):
+        self._ck(self._L.cdg_step_record(self.h, _ptr(d_u), _ptr(d_rec)), "cdg_step_record")
+
+    def cdg_step_adjoint_recorded(self, d_rec, d_lam_next, d_lam, d_gtau=None):
+        self._ck(self._L.cdg_step_adjoint_recorded(self.h, _ptr(d_rec), _ptr(d_lam_next), _ptr(d_lam), _ptr(d_gtau)),
+                 "cdg_step_adjoint_recorded")
 
     def cdg_get_time(self) -> float:
         t = ctypes.c_double()
