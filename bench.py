@@ -400,6 +400,10 @@ def run_adjoint(args, ws, rank, local):
         target = target[:, 0].clone()
         u0 = base + torch.from_numpy(W.perturbation(tuple(base.shape), args.seed + 1, 1e-3)).cuda()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        # warm-up of both paths (module load, adjoint scratch allocation)
+        wu = u0.clone().requires_grad_(True)
+        (rollout(wu, ctx, max(args.warmup, 1)) ** 2).sum().backward()
+        del wu
         # plain forward
         x = u0.clone()
         torch.cuda.synchronize()

@@ -30,6 +30,9 @@
 namespace oecdg {
 
 constexpr int AT = 128;  // threads per block of the per-cell adjoint kernels
+#ifndef OECDG_ADJ_ROLLED
+#define OECDG_ADJ_ROLLED 1
+#endif
 
 // w_bar += J1(w)^T fb1 + J2(w)^T fb2 for the 2D Euler flux at the conserved
 // state w = (rho, m, n, E) (m = rho u, n = rho v).
@@ -136,6 +139,7 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
       }
 
   const int oj0 = wrap_index<BC_PERIODIC>(jc + off, g.ny), oj1 = wrap_index<BC_PERIODIC>(jc + 1 + off, g.ny);
+#if OECDG_ADJ_ROLLED
   // the four sub-cells one after the other (not unrolled: keeps the live
   // registers of one sub-cell only)
 #pragma unroll 1
@@ -143,6 +147,15 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
     const int sx = s4 & 1, sy = s4 >> 1;
     const int oi = wrap_index<BC_PERIODIC>(ic + sx + off, g.nx);
     {
+#else
+  // the sub-cells one after the other: sx not unrolled (keeps the live
+  // registers of one sub-cell only), sy unrolled (its quadrature constants fold)
+#pragma unroll 1
+  for (int sx = 0; sx < 2; ++sx) {
+    const int oi = wrap_index<BC_PERIODIC>(ic + sx + off, g.nx);
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy) {
+#endif
       // contributions to the overlapping cell O(sx, sy)
       double Wb[F][9];
 #pragma unroll
@@ -487,88 +500,20 @@ __device__ __forceinline__ void beta_and_grad(const Geo& g, const double* w, dou
   }
 }
 
-// Forward sums S[n][m] of one field (n: face direction, m: derivative order),
-// the same arithmetic as oe_cell2d.
-__device__ __forceinline__ void oe_face_sums(const Geo& g, const double* u, const double* __restrict__ uo_f,
-                                             const int* oi, const int* oj, double (&S)[2][3]) {
+// Reverse of one derivative order M of the face sums of one field: given the
+// adjoints Sbx, Sby of S[x][M], S[y][M], add the adjoints of the cell's own
+// modes (ub[9]) and of the 4 overlapping cells' modes (wb[sx + 2 sy][9]).
+// Only the series order M needs is formed: M = 0 the value, M = 1 the value
+// and first normal derivative, M = 2 all three.
+template <int M>
+__device__ __forceinline__ void oe_order_vjp(const Geo& g, const double* u, const double* __restrict__ uo_f,
+                                             const int* oi, const int* oj, double Sbx, double Sby, double* ub,
+                                             double (&wb)[4][9]) {
   const long long P = g.plane;
   const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;
 #pragma unroll
   for (int n = 0; n < 2; ++n) {
-    S[n][0] = S[n][1] = S[n][2] = 0.0;
-    const double dn1 = n == 0 ? dx1 : dy1, dt1 = n == 0 ? dy1 : dx1;
-    const double dn2 = dn1 * dn1, dt2 = dt1 * dt1;
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const double s = 2.0 * side - 1.0;
-      double c0[3], c1[3], c2[3];
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const double u0 = n == 0 ? u[t * 3] : u[t], u1 = n == 0 ? u[t * 3 + 1] : u[3 + t];
-        const double u2 = n == 0 ? u[t * 3 + 2] : u[6 + t];
-        c0[t] = u0 + s * u1 + u2;
-        c1[t] = fma(3.0 * s, u2, u1);
-        c2[t] = 3.0 * u2;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const double dl = 1.0 - 2.0 * h;
-        const double* co = uo_f + (long long)(n == 0 ? oj[h] : oj[side]) * g.nx + (n == 0 ? oi[side] : oi[h]);
-        double w0[3], w1[3], w2[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          w0[t] = co[(n == 0 ? t * 3 : t) * P];
-          w1[t] = co[(n == 0 ? t * 3 + 1 : 3 + t) * P];
-          w2[t] = co[(n == 0 ? t * 3 + 2 : 6 + t) * P];
-        }
-        double o0[3], o2[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          o0[t] = fma(-0.5, w2[t], w0[t]);
-          o2[t] = 3.0 * w2[t];
-        }
-        double e0[3], e1[3], e2[3];
-        e0[2] = c0[2] - o0[2];
-        e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
-        e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
-        e1[2] = c1[2] - w1[2];
-        e1[1] = c1[1] - fma(3.0 * dl, w1[2], w1[1]);
-        e1[0] = c1[0] - fma(1.5, w1[2], fma(dl, w1[1], w1[0]));
-        e2[2] = c2[2] - o2[2];
-        e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
-        e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
-        const double a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
-        const double b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
-        const double t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
-        const double m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
-        const double tt = 3.0 * dt2 * e0[2];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const double ts = xs_self(h, q), p2 = lp(2, ts);
-          const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));
-          const double gn = fma(p2, a2, fma(ts, a1, a0));
-          const double gt = fma(ts, t1, t0);
-          const double hn = fma(p2, b2, fma(ts, b1, b0));
-          const double hm = fma(ts, m1, m0);
-          S[n][0] = fma(gwt(q), fabs(v), S[n][0]);
-          S[n][1] = fma(gwt(q), sqrt(fma(gn, gn, gt * gt)), S[n][1]);
-          S[n][2] = fma(gwt(q), sqrt(fma(hn, hn, fma(hm, hm, tt * tt))), S[n][2]);
-        }
-      }
-    }
-  }
-}
-
-// Reverse of oe_face_sums for one field: given Sb[n][m], add the adjoints of
-// the cell's own modes (ub[9]) and of the 4 overlapping cells' modes
-// (wb[sx + 2 sy][9]).
-__device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, const double* __restrict__ uo_f,
-                                                 const int* oi, const int* oj, const double (&Sb)[2][3],
-                                                 double* ub, double (&wb)[4][9]) {
-  const long long P = g.plane;
-  const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;
-#pragma unroll
-  for (int n = 0; n < 2; ++n) {
+    const double Sb = n == 0 ? Sbx : Sby;
     const double dn1 = n == 0 ? dx1 : dy1, dt1 = n == 0 ? dy1 : dx1;
     const double dn2 = dn1 * dn1, dt2 = dt1 * dt1;
 #pragma unroll
@@ -597,50 +542,46 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
           w1[t] = co[(n == 0 ? t * 3 + 1 : 3 + t) * P];
           w2[t] = co[(n == 0 ? t * 3 + 2 : 6 + t) * P];
         }
-        double o0[3], o2[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          o0[t] = fma(-0.5, w2[t], w0[t]);
-          o2[t] = 3.0 * w2[t];
+        double e0[3], e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+        {
+          const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
+          e0[2] = c0[2] - o0[2];
+          e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
+          e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
         }
-        double e0[3], e1[3], e2[3];
-        e0[2] = c0[2] - o0[2];
-        e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
-        e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
-        e1[2] = c1[2] - w1[2];
-        e1[1] = c1[1] - fma(3.0 * dl, w1[2], w1[1]);
-        e1[0] = c1[0] - fma(1.5, w1[2], fma(dl, w1[1], w1[0]));
-        e2[2] = c2[2] - o2[2];
-        e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
-        e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
-        const double a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
-        const double b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
-        const double t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
-        const double m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
-        const double tt = 3.0 * dt2 * e0[2];
-        double e0b[3] = {0, 0, 0}, a0b = 0, a1b = 0, a2b = 0, b0b = 0, b1b = 0, b2b = 0;
-        double t0b = 0, t1b = 0, m0b = 0, m1b = 0, ttb = 0;
-        // only the derivative orders whose adjoint is non-zero (the field
-        // gives the max of delta^m for those m only)
-        if (Sb[n][0] != 0.0) {
+        if (M >= 1) {
+          e1[2] = c1[2] - w1[2];
+          e1[1] = c1[1] - fma(3.0 * dl, w1[2], w1[1]);
+          e1[0] = c1[0] - fma(1.5, w1[2], fma(dl, w1[1], w1[0]));
+        }
+        if (M == 2) {
+          const double o2[3] = {3.0 * w2[0], 3.0 * w2[1], 3.0 * w2[2]};
+          e2[2] = c2[2] - o2[2];
+          e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
+          e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
+        }
+        double e0b[3] = {0, 0, 0}, e1b[3] = {0, 0, 0}, e2b[3] = {0, 0, 0};
+        if (M == 0) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const double ts = xs_self(h, q), p2 = lp(2, ts);
             const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));
-            const double vb = gwt(q) * Sb[n][0] * (v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0));
+            const double vb = gwt(q) * Sb * (v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0));
             e0b[0] += vb;
             e0b[1] += ts * vb;
             e0b[2] += p2 * vb;
           }
-        }
-        if (Sb[n][1] != 0.0) {
+        } else if (M == 1) {
+          const double a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
+          const double t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
+          double a0b = 0, a1b = 0, a2b = 0, t0b = 0, t1b = 0;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const double ts = xs_self(h, q), p2 = lp(2, ts);
             const double gn = fma(p2, a2, fma(ts, a1, a0));
             const double gt = fma(ts, t1, t0);
             const double r1 = sqrt(fma(gn, gn, gt * gt));
-            const double k1 = r1 > 0.0 ? gwt(q) * Sb[n][1] / r1 : 0.0;
+            const double k1 = r1 > 0.0 ? gwt(q) * Sb / r1 : 0.0;
             const double gnb = k1 * gn, gtb = k1 * gt;
             a0b += gnb;
             a1b += ts * gnb;
@@ -648,15 +589,24 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
             t0b += gtb;
             t1b += ts * gtb;
           }
-        }
-        if (Sb[n][2] != 0.0) {
+          e0b[1] += dt1 * t0b;
+          e0b[2] += 3.0 * dt1 * t1b;
+          e1b[0] = dn1 * a0b;
+          e1b[1] = dn1 * a1b;
+          e1b[2] = dn1 * a2b;
+        } else {
+          const double a1 = dn1 * e1[1], a2 = dn1 * e1[2];
+          const double b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
+          const double m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
+          const double tt = 3.0 * dt2 * e0[2];
+          double b0b = 0, b1b = 0, b2b = 0, m0b = 0, m1b = 0, ttb = 0;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const double ts = xs_self(h, q), p2 = lp(2, ts);
             const double hn = fma(p2, b2, fma(ts, b1, b0));
             const double hm = fma(ts, m1, m0);
             const double r2 = sqrt(fma(hn, hn, fma(hm, hm, tt * tt)));
-            const double k2 = r2 > 0.0 ? gwt(q) * Sb[n][2] / r2 : 0.0;
+            const double k2 = r2 > 0.0 ? gwt(q) * Sb / r2 : 0.0;
             const double hnb = k2 * hn, hmb = k2 * hm;
             ttb += k2 * tt;
             b0b += hnb;
@@ -665,31 +615,23 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
             m0b += hmb;
             m1b += ts * hmb;
           }
+          e0b[2] += 3.0 * dt2 * ttb;
+          e1b[1] = dn1 * dt1 * m0b;
+          e1b[2] = dn1 * 3.0 * dt1 * m1b;
+          e2b[0] = dn2 * b0b;
+          e2b[1] = dn2 * b1b;
+          e2b[2] = dn2 * b2b;
         }
-        // back through the scalings
-        e0b[1] += dt1 * t0b;
-        e0b[2] += 3.0 * dt1 * t1b + 3.0 * dt2 * ttb;
-        a1b += dt1 * m0b;
-        a2b += 3.0 * dt1 * m1b;
-        const double e1b[3] = {dn1 * a0b, dn1 * a1b, dn1 * a2b};
-        const double e2b[3] = {dn2 * b0b, dn2 * b1b, dn2 * b2b};
         // e = c - shift(o): c_bar += e_bar; o_bar = -shift^T e_bar
-        double o0b[3], o1b[3], o2b[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           c0b[t] += e0b[t];
           c1b[t] += e1b[t];
           c2b[t] += e2b[t];
         }
-        o0b[0] = -e0b[0];
-        o0b[1] = -(dl * e0b[0] + e0b[1]);
-        o0b[2] = -(1.5 * e0b[0] + 3.0 * dl * e0b[1] + e0b[2]);
-        o1b[0] = -e1b[0];
-        o1b[1] = -(dl * e1b[0] + e1b[1]);
-        o1b[2] = -(1.5 * e1b[0] + 3.0 * dl * e1b[1] + e1b[2]);
-        o2b[0] = -e2b[0];
-        o2b[1] = -(dl * e2b[0] + e2b[1]);
-        o2b[2] = -(1.5 * e2b[0] + 3.0 * dl * e2b[1] + e2b[2]);
+        const double o0b[3] = {-e0b[0], -(dl * e0b[0] + e0b[1]), -(1.5 * e0b[0] + 3.0 * dl * e0b[1] + e0b[2])};
+        const double o1b[3] = {-e1b[0], -(dl * e1b[0] + e1b[1]), -(1.5 * e1b[0] + 3.0 * dl * e1b[1] + e1b[2])};
+        const double o2b[3] = {-e2b[0], -(dl * e2b[0] + e2b[1]), -(1.5 * e2b[0] + 3.0 * dl * e2b[1] + e2b[2])};
         // o0 = w0 - w2/2, o1 = w1, o2 = 3 w2
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
@@ -707,17 +649,6 @@ __device__ __forceinline__ void oe_face_sums_vjp(const Geo& g, const double* u, 
       }
     }
   }
-}
-
-// Forward OE step that also records (delta^m, field of the max, its face
-// sums) per cell for the adjoint.
-template <int SYS>
-__global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
-                                                 const double* __restrict__ dt, const double* __restrict__ sigma,
-                                                 int* __restrict__ status, double* __restrict__ rec) {
-  oe_cell2d<SYS, BC_PERIODIC, false, 1>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
-                                         blockIdx.x * 32 + (threadIdx.x & 31),
-                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec);
 }
 
 // Adjoint of the OE step of one cell from its record: lam_h[K] (own modes)
@@ -787,51 +718,53 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
   const double r1b = -tau * e1 * e1b, r2b = -tau * e2 * e2b;
   double t_acc = -(r1 * e1 * e1b + r2 * e2 * e2b);
   const double db[3] = {r1b + r2b, r1b + r2b, r2b};
-  // delta^m = delta^m(arg[m]) = (bx cx Sx + by cy Sy) / sigma
+  // delta^m = delta^m(arg[m]) = (bx cx Sx + by cy Sy) / sigma: one reverse pass
+  // per order m on the field that gives its max (the field is data, so the
+  // lanes of a warp follow the same path whatever field each one has)
   double bxb = 0.0, byb = 0.0;
   double sigb[F];
-#pragma unroll 1
-  for (int f = 0; f < F; ++f) {
-    sigb[f] = 0.0;
-    double Sb[2][3];
-    bool any = false;
-    const double sg = stats[(mesh * F + f) * 6 + 5];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      Sb[0][m] = Sb[1][m] = 0.0;
-      if (arg[m] == f && active) {
-        const double k = db[m] / sg;
-        Sb[0][m] = k * bx * cx[m];
-        Sb[1][m] = k * by * cy[m];
-        bxb += k * cx[m] * Sxm[m];
-        byb += k * cy[m] * Sym[m];
-        sigb[f] -= db[m] * d[m] / sg;
-        any = true;
-      }
+  for (int f = 0; f < F; ++f) sigb[f] = 0.0;
+  if (active) {
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      double* sl = slots + slot_off(numel, s4) + self;
+#pragma unroll
+      for (int q = 0; q < F * 9; ++q) sl[q * P] = 0.0;
     }
-    double wbl[4][9];
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int f = arg[m];
+    if (f < 0 || !active) continue;
+    const double sg = stats[(mesh * F + f) * 6 + 5];
+    const double k = db[m] / sg;
+    bxb += k * cx[m] * Sxm[m];
+    byb += k * cy[m] * Sym[m];
+#pragma unroll
+    for (int ff = 0; ff < F; ++ff)
+      if (ff == f) sigb[ff] -= db[m] * d[m] / sg;
+    double u[9], ub[9], wbl[4][9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      u[q] = uh[self + (f * 9 + q) * P];
+      ub[q] = 0.0;
+    }
 #pragma unroll
     for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-      for (int m = 0; m < 9; ++m) wbl[s4][m] = 0.0;
-    if (any) {
-      double u[9], ub[9];
+      for (int q = 0; q < 9; ++q) wbl[s4][q] = 0.0;
+    const double* uof = uo + (long long)f * 9 * P;
+    if (m == 0) oe_order_vjp<0>(g, u, uof, oi, oj, k * bx * cx[0], k * by * cy[0], ub, wbl);
+    else if (m == 1) oe_order_vjp<1>(g, u, uof, oi, oj, k * bx * cx[1], k * by * cy[1], ub, wbl);
+    else oe_order_vjp<2>(g, u, uof, oi, oj, k * bx * cx[2], k * by * cy[2], ub, wbl);
 #pragma unroll
-      for (int m = 0; m < 9; ++m) {
-        u[m] = uh[self + (f * 9 + m) * P];
-        ub[m] = 0.0;
-      }
-      oe_face_sums_vjp(g, u, uo + f * 9 * P, oi, oj, Sb, ub, wbl);
+    for (int q = 0; q < 9; ++q) lamh[self + (f * 9 + q) * P] += ub[q];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) lamh[self + (f * 9 + m) * P] += ub[m];
-    }
-    if (active) {
+    for (int s4 = 0; s4 < 4; ++s4) {
+      double* sl = slots + slot_off(numel, s4) + self + (long long)f * 9 * P;
 #pragma unroll
-      for (int s4 = 0; s4 < 4; ++s4) {
-        double* sl = slots + slot_off(numel, s4) + self + (long long)f * 9 * P;
-#pragma unroll
-        for (int m = 0; m < 9; ++m) sl[m * P] = wbl[s4][m];
-      }
+      for (int q = 0; q < 9; ++q) sl[q * P] += wbl[s4][q];
     }
   }
   // beta at the cell average (mode 0)
