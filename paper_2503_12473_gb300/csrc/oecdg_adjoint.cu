@@ -500,6 +500,17 @@ __device__ __forceinline__ void beta_and_grad(const Geo& g, const double* w, dou
   }
 }
 
+// Forward OE step that also records (delta^m, field of the max, its face
+// sums) per cell for the adjoint.
+template <int SYS>
+__global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
+                                                 const double* __restrict__ dt, const double* __restrict__ sigma,
+                                                 int* __restrict__ status, double* __restrict__ rec) {
+  oe_cell2d<SYS, BC_PERIODIC, false, 1>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
+                                         blockIdx.x * 32 + (threadIdx.x & 31),
+                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec);
+}
+
 // Reverse of one derivative order M of the face sums of one field: given the
 // adjoints Sbx, Sby of S[x][M], S[y][M], add the adjoints of the cell's own
 // modes (ub[9]) and of the 4 overlapping cells' modes (wb[sx + 2 sy][9]).
