@@ -3,9 +3,13 @@
  * oscillation-eliminating central DG (OECDG) forward time step of
  * Peng, Wu, Yuan, arXiv:2503.12473.
  *
- * Scope of the CUDA path: degree k = 2 only -- the 1D space P^2 (= Q^2 in 1D) and
- * the 2D tensor space Q^2 -- for linear advection and the compressible Euler
- * equations, periodic or transmissive boundaries, forward Euler or SSP-RK3.
+ * Scope of the CUDA path:
+ *   - 2D: the tensor space Q^2, linear advection and the compressible Euler
+ *     equations, forward Euler, SSP-RK2 or SSP-RK3;
+ *   - 1D: P^k with k = 1, 2 or 3, linear advection, Burgers (f = u^2/2) and
+ *     the 1D Euler equations, forward Euler, SSP-RK2, SSP-RK3 or the classical
+ *     four-stage RK4 (written in Shu-Osher form, used for Table 2);
+ * both with periodic or transmissive boundaries.
  *
  * Conventions shared by every entry point
  *   - Every call returns a cdg_status; nothing throws, aborts or exits.
@@ -18,12 +22,12 @@
  *     (i+1, j+1)); field = conserved variable (Euler 2D: rho, rho u, rho v, E;
  *     1D: rho, rho v, E; advection: u); mode = Legendre mode (a,b) of the
  *     unnormalised Legendre polynomials P_a(xi) P_b(eta) at index b*3 + a in 2D,
- *     a in 1D.  j is absent (ny = 1) in 1D.
+ *     a = 0..k in 1D.  j is absent (ny = 1) in 1D.
  *   - All calls are asynchronous on the context's stream unless stated.
  *   - tau and tau_max live in device memory owned by the context, so that a
  *     sequence of cdg_step_async calls can be captured in a CUDA graph.
- *   - Scratch memory (two state-sized buffers, reduction partials) is owned by
- *     the context and allocated in cdg_init_mesh.
+ *   - Scratch memory (two state-sized buffers, four with RK4, and reduction
+ *     partials) is owned by the context and allocated in cdg_init_mesh.
  */
 #ifndef OECDG_H
 #define OECDG_H
@@ -47,18 +51,18 @@ typedef enum {
 enum { CDG_ADVECTION = 0, CDG_BURGERS = 1, CDG_EULER = 2 };
 enum { CDG_BASIS_Q = 0, CDG_BASIS_P = 1 };
 enum { CDG_PERIODIC = 0, CDG_TRANSMISSIVE = 1 };
-enum { CDG_RK_EULER1 = 1, CDG_RK_SSP3 = 3 };
+enum { CDG_RK_EULER1 = 1, CDG_RK_SSP2 = 2, CDG_RK_SSP3 = 3, CDG_RK_RK4 = 4 };
 
 /* Problem description (Section 2.1 meshes and spaces; Section 4 time stepping). */
 typedef struct {
   int dim;       /* 1 or 2 */
   int nx, ny;    /* primal cells per direction (ny is ignored when dim = 1) */
-  int k;         /* polynomial degree; the CUDA path supports k = 2 */
-  int basis;     /* CDG_BASIS_Q (1D: P^2 = Q^2) */
-  int system;    /* CDG_ADVECTION or CDG_EULER */
+  int k;         /* polynomial degree: 2 in 2D, 1..3 in 1D */
+  int basis;     /* CDG_BASIS_Q (1D: P^k = Q^k, either value accepted) */
+  int system;    /* CDG_ADVECTION, CDG_EULER, or (1D only) CDG_BURGERS */
   int bc;        /* CDG_PERIODIC or CDG_TRANSMISSIVE on every side */
   int oe;        /* 1: apply the OE step F_tau after every RK stage */
-  int rk;        /* CDG_RK_EULER1 or CDG_RK_SSP3 */
+  int rk;        /* CDG_RK_EULER1, _SSP2, _SSP3, or (1D only) CDG_RK_RK4 */
   int pad;
   double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
   double gamma;          /* ratio of specific heats (Euler) */
@@ -72,7 +76,8 @@ typedef struct cdg_ctx cdg_ctx;
  * `stream` (a cudaStream_t; NULL = the legacy default stream), on the current
  * device.  Allocates the geometry constants and the scratch buffers.
  * Errors: CDG_EINVAL (null pointers, sizes < 2, bad enums), CDG_EUNSUPPORTED
- * (k != 2, basis P in 2D, Burgers), CDG_ENOMEM, CDG_ECUDA.  On error *out is
+ * (2D: k != 2, basis P, Burgers or RK4; 1D: k outside 1..3), CDG_ENOMEM,
+ * CDG_ECUDA.  On error *out is
  * NULL. */
 cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out);
 
@@ -86,7 +91,7 @@ const char* cdg_last_error(const cdg_ctx* ctx);
 cdg_status cdg_state_numel(const cdg_ctx* ctx, size_t* numel);
 
 /* Sampling points of the projection-based initialisation (Section 3.3): on
- * every cell of both meshes, 3 x 3 (1D: 3) Gauss points on each of its 4
+ * every cell of both meshes, 3 x 3 (1D: k + 1) Gauss points on each of its 4
  * (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx] of (x, y) pairs (1D:
  * [mesh][i][sx][qx] of x).  With d_xy == NULL only *npts is set; otherwise
  * d_xy is a device array of npts * dim doubles. */
@@ -117,21 +122,37 @@ cdg_status cdg_set_dt(cdg_ctx* ctx, double tau, double tau_max);
 cdg_status cdg_get_dt(cdg_ctx* ctx, double* tau, double* tau_max);
 
 /* One RK stage of Eq. (eq:RKCDG) without the OE step, with the context's tau
- * and tau_max: SSP-RK3 stage l in {0,1,2}
- *     d_out = c_l d_un + (1 - c_l) (d_ul + tau L(d_ul)),  c = (0, 3/4, 1/3),
- * (forward Euler: l = 0 only).  d_out must not alias d_ul or d_un, except that
- * d_un is not read when l = 0. */
+ * and tau_max, in the Shu-Osher form of the context's method:
+ *   forward Euler   l = 0:        d_out = d_ul + tau L(d_ul)
+ *   SSP-RK2/SSP-RK3 l >= 1:       d_out = c_l d_un + (1 - c_l)(d_ul + tau L(d_ul)),
+ *                                 c = (0, 1/2) resp. (0, 3/4, 1/3)
+ *   RK4             l = 0, 1, 2:  d_out = d_un + a_l tau L(d_ul), a = (1/2, 1/2, 1)
+ *                                 (l = 0: d_un is d_ul and is not read)
+ * RK4's last stage combines four states: use cdg_rk_combine for it (l = 3 is
+ * CDG_EINVAL here).  d_out must not alias d_ul or d_un. */
 cdg_status cdg_rk_stage(cdg_ctx* ctx, int l, const double* d_un, const double* d_ul, double* d_out);
 
+/* A general Shu-Osher stage (Eq. (eq:RKCDG) with any explicit RK method):
+ *     d_out = sum_{m < n} coef[m] d_terms[m] + ct tau L(d_ul),
+ * n in 1..4, d_terms a HOST array of n device state pointers, coef a host
+ * array of n doubles.  Classical RK4's last stage is n = 4 with terms
+ * (u^n, u^(1), u^(2), u^(3)), coef (-1/3, 1/3, 2/3, 1/3), ct = 1/6 and
+ * d_ul = u^(3).  In 2D only the two-state form (n = 2, d_terms[1] == d_ul,
+ * coef[1] == ct, or n = 1, d_terms[0] == d_ul, coef[0] == ct == 1) runs;
+ * other forms return CDG_EUNSUPPORTED there.  d_out must not alias d_ul or
+ * any term. */
+cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double* const* d_terms, const double* coef,
+                          double ct, double* d_out);
+
 /* The OE step u_sigma = F_tau u_h (Eq. (OEstep2D), solved exactly): sigma_K
- * and avg per mesh and field, the damping coefficients delta_K^m (m = 0..2)
+ * and avg per mesh and field, the damping coefficients delta_K^m (m = 0..k)
  * from the traces of u^C - u^D on the half-faces of every cell, the wave speed
  * beta_{e,K} at the cell average, and the exponential decay of every mode of
  * total degree >= 1.  tau from the context.  d_usig must not alias d_uh.
  * A non-physical cell average sets the context's status flag. */
 cdg_status cdg_oe_damp(cdg_ctx* ctx, const double* d_uh, double* d_usig);
 
-/* The damping coefficients alone, for inspection: d_delta [2][ny][nx][3],
+/* The damping coefficients alone, for inspection: d_delta [2][ny][nx][k+1],
  * d_sigma [2][fields] (either may be NULL). */
 cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta, double* d_sigma);
 

@@ -1,9 +1,12 @@
-// oecdg_1d.cu -- 1D P^2 kernels of the OECDG forward step (arXiv:2503.12473),
-// Eq. (eq:1D_H) and the 1D form of the damping coefficients (Remark in
-// Section 2.2).  One thread per cell of one mesh (blockIdx.y = mesh); primal
-// cell i overlaps dual cells i-1 (left half) and i (right half), dual cell i
-// overlaps primal cells i and i+1; in the overlapping cell the point xi of
-// half s sits at xi' = xi + 1 - 2 s.
+// oecdg_1d.cu -- 1D P^K kernels (K = 1, 2, 3) of the OECDG forward step
+// (arXiv:2503.12473): Eq. (eq:1D_H) and the 1D form of the damping
+// coefficients (Remark in Section 2.2), for linear advection, Burgers
+// (f = u^2/2) and the 1D Euler equations.  One thread per cell of one mesh
+// (blockIdx.y = mesh); primal cell i overlaps dual cells i-1 (left half) and i
+// (right half), dual cell i overlaps primal cells i and i+1; in the overlapping
+// cell the point xi of half s sits at xi' = xi + 1 - 2 s.
+#include <type_traits>
+
 #include "oecdg_common.cuh"
 #include "oecdg_kernels.h"
 
@@ -11,6 +14,37 @@ namespace oecdg {
 
 constexpr int NT1 = 128;
 constexpr double DINF1 = __builtin_huge_val();
+
+// (K+1)-point Gauss-Legendre rules on [-1, 1], nodes in increasing order:
+//  2 points: +-1/sqrt(3), weights 1;
+//  3 points: 0, +-sqrt(3/5), weights 8/9, 5/9;
+//  4 points: +-sqrt(3/7 -+ (2/7) sqrt(6/5)), weights (18 +- sqrt(30)) / 36.
+__host__ __device__ constexpr double gn1(int N, int q) {
+  return N == 2 ? (q == 0 ? -0.57735026918962576451 : 0.57735026918962576451)
+       : N == 3 ? gnode(q)
+       : (q == 0 ? -0.86113631159405257522
+          : q == 1 ? -0.33998104358485626480 : q == 2 ? 0.33998104358485626480 : 0.86113631159405257522);
+}
+__host__ __device__ constexpr double gw1(int N, int q) {
+  return N == 2 ? 1.0
+       : N == 3 ? gwt(q)
+       : ((q == 0 || q == 3) ? 0.34785484513745385737 : 0.65214515486254614263);
+}
+
+// d-th derivative of the unnormalised Legendre polynomial P_n (n <= 3)
+__host__ __device__ constexpr double lpd(int n, int d, double x) {
+  return d == 0 ? (n == 0 ? 1.0 : n == 1 ? x : n == 2 ? 1.5 * x * x - 0.5 : (2.5 * x * x - 1.5) * x)
+       : d == 1 ? (n == 0 ? 0.0 : n == 1 ? 1.0 : n == 2 ? 3.0 * x : 7.5 * x * x - 1.5)
+       : d == 2 ? (n < 2 ? 0.0 : n == 2 ? 3.0 : 15.0 * x)
+       : d == 3 ? (n == 3 ? 15.0 : 0.0)
+       : 0.0;
+}
+__host__ __device__ constexpr double fact(int m) { return m <= 1 ? 1.0 : m * fact(m - 1); }
+
+// points of half s in the cell's own reference coordinate and in the
+// overlapping cell (N-point rule)
+__host__ __device__ constexpr double xs1(int N, int s, int q) { return s - 0.5 + 0.5 * gn1(N, q); }
+__host__ __device__ constexpr double xo1(int N, int s, int q) { return 0.5 - s + 0.5 * gn1(N, q); }
 
 template <int SYS>
 struct Fields1 {
@@ -26,57 +60,81 @@ __device__ __forceinline__ void flux1(const Geo& g, const double* w, double* f) 
     f[0] = w[1];
     f[1] = fma(w[1], v, p);
     f[2] = (w[2] + p) * v;
+  } else if (SYS == SYS_BURGERS) {
+    f[0] = 0.5 * w[0] * w[0];
   } else {
     f[0] = g.adv_x * w[0];
   }
 }
 
+// Wave speed |f'(w)| (Euler: |v| + c); -1 for a non-physical Euler state.
+template <int SYS>
+__device__ __forceinline__ double speed1(const Geo& g, const double* w) {
+  if (SYS == SYS_EULER) {
+    const double v = w[1] / w[0];
+    const double p = (g.gamma - 1.0) * (w[2] - 0.5 * w[1] * v);
+    if (!(w[0] > 0.0 && p > 0.0)) return -1.0;
+    return fabs(v) + sqrt(g.gamma * p / w[0]);
+  } else if (SYS == SYS_BURGERS) {
+    return fabs(w[0]);
+  }
+  return fabs(g.adv_x);
+}
+
 // L_a = (2a+1) [ sum_{s,q} (w_q/4)(w/tau_max) P_a(xi) + (1/h) sum (w_q/2) f(w) P_a'(xi)
 //               - (1/h)(f_R - (-1)^a f_L) ] - u_a / tau_max
-template <int SYS, int BC>
+template <int SYS, int BC, int K>
 __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restrict__ u, int mesh, int i, double inv_tm,
-                                           double (&L)[Fields1<SYS>::F][3]) {
-  constexpr int F = Fields1<SYS>::F;
+                                           double (&L)[Fields1<SYS>::F][K + 1]) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
   const long long P = g.plane;
-  const double* uo = u + (long long)(1 - mesh) * F * 3 * P;
-  const double* us = u + (long long)mesh * F * 3 * P + i;
+  const double* uo = u + (long long)(1 - mesh) * F * M * P;
+  const double* us = u + (long long)mesh * F * M * P + i;
   const int off = mesh == 0 ? -1 : 0;
-  double Ad[F][3], Bd[F][3];  // dissipation and flux-gradient sums
+  double Ad[F][M], Bd[F][M];  // dissipation and flux-gradient sums
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) Ad[f][a] = Bd[f][a] = 0.0;
+    for (int a = 0; a < M; ++a) Ad[f][a] = Bd[f][a] = 0.0;
   double fL[F], fR[F];
 #pragma unroll
   for (int sx = 0; sx < 2; ++sx) {
     const double* c = uo + wrap_index<BC>(i + sx + off, g.nx);
-    double w0[F], w1[F], w2[F];
+    double w[F][M];
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-      w0[f] = __ldg(c + (f * 3) * P);
-      w1[f] = __ldg(c + (f * 3 + 1) * P);
-      w2[f] = __ldg(c + (f * 3 + 2) * P);
-    }
+    for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double xo = xs_other(sx, q), xsf = xs_self(sx, q);
+      for (int a = 0; a < M; ++a) w[f][a] = __ldg(c + (f * M + a) * P);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const double xo = xo1(N, sx, q), xsf = xs1(N, sx, q);
       double V[F], fl[F];
 #pragma unroll
-      for (int f = 0; f < F; ++f) V[f] = fma(lp(2, xo), w2[f], fma(xo, w1[f], w0[f]));
+      for (int f = 0; f < F; ++f) {
+        double v = w[f][0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) v = fma(lpd(a, 0, xo), w[f][a], v);
+        V[f] = v;
+      }
       flux1<SYS>(g, V, fl);
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        Ad[f][0] = fma(gwt(q), V[f], Ad[f][0]);
-        Ad[f][1] = fma(gwt(q) * xsf, V[f], Ad[f][1]);
-        Ad[f][2] = fma(gwt(q) * lp(2, xsf), V[f], Ad[f][2]);
-        Bd[f][1] = fma(gwt(q), fl[f], Bd[f][1]);
-        Bd[f][2] = fma(gwt(q) * dlp(2, xsf), fl[f], Bd[f][2]);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          Ad[f][a] = fma(gw1(N, q) * lpd(a, 0, xsf), V[f], Ad[f][a]);
+          if (a > 0) Bd[f][a] = fma(gw1(N, q) * lpd(a, 1, xsf), fl[f], Bd[f][a]);
+        }
       }
     }
     // face of this half: the overlapping cell's centre (xi' = 0)
     double V[F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) V[f] = fma(-0.5, w2[f], w0[f]);
+    for (int f = 0; f < F; ++f) {
+      double v = w[f][0];
+#pragma unroll
+      for (int a = 2; a < M; a += 2) v = fma(lpd(a, 0, 0.0), w[f][a], v);
+      V[f] = v;
+    }
     if (sx) flux1<SYS>(g, V, fR);
     else flux1<SYS>(g, V, fL);
   }
@@ -84,54 +142,63 @@ __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restric
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < M; ++a) {
       const double face = fR[f] - ((a & 1) ? -fL[f] : fL[f]);
       const double br = 0.25 * inv_tm * Ad[f][a] + ih * (0.5 * Bd[f][a] - face);
-      L[f][a] = fma((double)(2 * a + 1), br, -inv_tm * __ldg(us + (f * 3 + a) * P));
+      L[f][a] = fma((double)(2 * a + 1), br, -inv_tm * __ldg(us + (f * M + a) * P));
     }
 }
 
 enum { MODE1_RHS = 0, MODE1_STAGE = 1 };
 
-template <int SYS, int BC, int MODE>
-__global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict__ uin, const double* __restrict__ un,
-                                                 double* __restrict__ out, const double* __restrict__ dt, double ca,
-                                                 double cb, double* __restrict__ partials) {
-  constexpr int F = Fields1<SYS>::F;
+// MODE1_RHS:   out = L(uin).
+// MODE1_STAGE: out = sum_m cb.c[m] cb.u[m] + cb.ct tau L(uin)  (one Shu-Osher
+//              stage), plus per-block sigma partials of out: sum of the cell
+//              averages and max / min over the cell's K+1 Gauss points.
+template <int SYS, int BC, int K, int MODE>
+__global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict__ uin, StageComb cb,
+                                                 double* __restrict__ out, const double* __restrict__ dt,
+                                                 double* __restrict__ partials) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
   const int mesh = blockIdx.y;
   const int i = blockIdx.x * NT1 + threadIdx.x;
   const bool active = i < g.nx;
   const int ic = active ? i : 0;
   const double tau = dt[0], tm = dt[1];
   const double inv_tm = 1.0 / tm;
-  double L[F][3];
-  cell_rhs1d<SYS, BC>(g, uin, mesh, ic, inv_tm, L);
+  double L[F][M];
+  cell_rhs1d<SYS, BC, K>(g, uin, mesh, ic, inv_tm, L);
   const long long P = g.plane;
-  const long long base = (long long)mesh * F * 3 * P + ic;
+  const long long base = (long long)mesh * F * M * P + ic;
   if (MODE == MODE1_RHS) {
     if (active)
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) out[base + (f * 3 + a) * P] = L[f][a];
+        for (int a = 0; a < M; ++a) out[base + (f * M + a) * P] = L[f][a];
     return;
   } else {
     __shared__ double sh[96];
+    const double tl = cb.ct * tau;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-      double v[3];
+      double v[M];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const long long id = base + (f * 3 + a) * P;
-        double s = fma(tau, L[f][a], __ldg(uin + id));
-        if (ca != 0.0) s = fma(ca, __ldg(un + id), cb * s);
+      for (int a = 0; a < M; ++a) {
+        const long long id = base + (f * M + a) * P;
+        double s = tl * L[f][a];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m < cb.n) s = fma(cb.c[m], __ldg(cb.u[m] + id), s);
         v[a] = s;
         if (active) out[id] = s;
       }
       double mx = -DINF1, mn = DINF1;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const double val = fma(lp(2, gnode(q)), v[2], fma(gnode(q), v[1], v[0]));
+      for (int q = 0; q < N; ++q) {
+        double val = v[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) val = fma(lpd(a, 0, gn1(N, q)), v[a], val);
         mx = fmax(mx, val);
         mn = fmin(mn, val);
       }
@@ -152,99 +219,113 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
   }
 }
 
-// delta^m = (2m+1) h^{m-1} / ((2k-1) m!) beta (|d^m (u^C-u^D)|_R + |...|_L) / sigma,
-// max over fields; then the exact damping of the modes of degree 1 and 2.
-template <int SYS, int BC, bool WRITE_DELTA>
+// delta^m = (2m+1) h^{m-1} / ((2K-1) m!) beta (|d^m (u^C-u^D)|_R + |...|_L) / sigma
+// for m = 0..K, max over fields; then the exact damping of mode a by
+// exp(-tau sum_{m <= a} delta^m).  The face points are the cell ends xi = +-1,
+// which are the centres (xi' = 0) of the two overlapping cells.
+template <int SYS, int BC, int K, bool WRITE_DELTA>
 __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                               const double* __restrict__ dt, const double* __restrict__ sigma,
                                               double* __restrict__ delta_out, int* __restrict__ status) {
-  constexpr int F = Fields1<SYS>::F;
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
   const int mesh = blockIdx.y;
   const int i = blockIdx.x * NT1 + threadIdx.x;
   if (i >= g.nx) return;
   const long long P = g.plane;
-  const double* us = uh + (long long)mesh * F * 3 * P + i;
-  const double* uo = uh + (long long)(1 - mesh) * F * 3 * P;
+  const double* us = uh + (long long)mesh * F * M * P + i;
+  const double* uo = uh + (long long)(1 - mesh) * F * M * P;
   const int off = mesh == 0 ? -1 : 0;
   const int oL = wrap_index<BC>(i + off, g.nx), oR = wrap_index<BC>(i + 1 + off, g.nx);
-  double beta;
-  if (SYS == SYS_EULER) {
-    const double rho = __ldg(us), m = __ldg(us + 3 * P), E = __ldg(us + 6 * P);
-    const double v = m / rho;
-    const double p = (g.gamma - 1.0) * (E - 0.5 * m * v);
-    if (rho > 0.0 && p > 0.0) {
-      beta = fabs(v) + sqrt(g.gamma * p / rho);
-    } else {
-      atomicOr(status, ST_NONPHYSICAL);
-      beta = 0.0;
-    }
-  } else {
-    beta = fabs(g.adv_x);
+  double wa[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) wa[f] = __ldg(us + (f * M) * P);
+  double beta = speed1<SYS>(g, wa);
+  if (beta < 0.0) {
+    atomicOr(status, ST_NONPHYSICAL);
+    beta = 0.0;
   }
-  const double h = g.hx, d1 = 2.0 / h, d2 = d1 * d1;
-  // (2m+1) h^{m-1} / ((2k-1) m!), k = 2
-  const double k0 = 1.0 / (3.0 * h), k1 = 1.0, k2 = 5.0 * h / 6.0;
-  double dl0 = 0.0, dl1 = 0.0, dl2 = 0.0;
+  const double h = g.hx, d1 = 2.0 / h;
+  double km[M];  // (2m+1) h^{m-1} / ((2K-1) m!) (2/h)^m
+  {
+    double hp = 1.0 / h, dp = 1.0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      km[m] = (2 * m + 1) * hp * dp / ((2 * K - 1) * fact(m));
+      hp *= h;
+      dp *= d1;
+    }
+  }
+  double dl[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) dl[m] = 0.0;
 #pragma unroll
   for (int f = 0; f < F; ++f) {
     const double sg = __ldg(sigma + mesh * F + f);
-    const double u0 = __ldg(us + (f * 3) * P), u1 = __ldg(us + (f * 3 + 1) * P), u2 = __ldg(us + (f * 3 + 2) * P);
-    const double* cl = uo + (f * 3) * P + oL;
-    const double* cr = uo + (f * 3) * P + oR;
-    const double l0 = __ldg(cl), l1 = __ldg(cl + P), l2 = __ldg(cl + 2 * P);
-    const double r0 = __ldg(cr), r1 = __ldg(cr + P), r2 = __ldg(cr + 2 * P);
-    // right face xi = 1 (overlapping cell oR at its centre), left face xi = -1 (oL)
-    const double jr0 = fabs((u0 + u1 + u2) - fma(-0.5, r2, r0));
-    const double jl0 = fabs((u0 - u1 + u2) - fma(-0.5, l2, l0));
-    const double jr1 = fabs(d1 * (fma(3.0, u2, u1) - r1));
-    const double jl1 = fabs(d1 * (fma(-3.0, u2, u1) - l1));
-    const double jr2 = fabs(d2 * 3.0 * (u2 - r2));
-    const double jl2 = fabs(d2 * 3.0 * (u2 - l2));
+    double u[M], l[M], r[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      u[a] = __ldg(us + (f * M + a) * P);
+      l[a] = __ldg(uo + (f * M + a) * P + oL);
+      r[a] = __ldg(uo + (f * M + a) * P + oR);
+    }
     if (sg != 0.0) {
       const double is = beta / sg;
-      dl0 = fmax(dl0, k0 * (jr0 + jl0) * is);
-      dl1 = fmax(dl1, k1 * (jr1 + jl1) * is);
-      dl2 = fmax(dl2, k2 * (jr2 + jl2) * is);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        // reference-coordinate m-th derivatives: own trace at xi = +-1, other at 0
+        double jr = 0.0, jl = 0.0;
+#pragma unroll
+        for (int a = m; a < M; ++a) {
+          const double o = lpd(a, m, 0.0);
+          jr = fma(lpd(a, m, 1.0), u[a], jr);
+          jr = fma(-o, r[a], jr);
+          jl = fma(lpd(a, m, -1.0), u[a], jl);
+          jl = fma(-o, l[a], jl);
+        }
+        dl[m] = fmax(dl[m], km[m] * (fabs(jr) + fabs(jl)) * is);
+      }
     }
   }
   if (WRITE_DELTA) {
-    double* dp = delta_out + ((long long)mesh * g.nx + i) * 3;
-    dp[0] = dl0;
-    dp[1] = dl1;
-    dp[2] = dl2;
+    double* dp = delta_out + ((long long)mesh * g.nx + i) * M;
+#pragma unroll
+    for (int m = 0; m < M; ++m) dp[m] = dl[m];
   }
   if (usig != nullptr) {
     const double tau = dt[0];
-    const double e1 = exp(-tau * (dl0 + dl1)), e2 = exp(-tau * (dl0 + dl1 + dl2));
-    double* os = usig + (long long)mesh * F * 3 * P + i;
+    double e[M];
+    double rate = dl[0];
+#pragma unroll
+    for (int a = 1; a < M; ++a) {
+      rate += dl[a];
+      e[a] = exp(-tau * rate);
+    }
+    double* os = usig + (long long)mesh * F * M * P + i;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-      os[(f * 3) * P] = __ldg(us + (f * 3) * P);
-      os[(f * 3 + 1) * P] = __ldg(us + (f * 3 + 1) * P) * e1;
-      os[(f * 3 + 2) * P] = __ldg(us + (f * 3 + 2) * P) * e2;
+      os[(f * M) * P] = __ldg(us + (f * M) * P);
+#pragma unroll
+      for (int a = 1; a < M; ++a) os[(f * M + a) * P] = __ldg(us + (f * M + a) * P) * e[a];
     }
   }
 }
 
-template <int SYS>
+template <int SYS, int K>
 __global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict__ partial, int* __restrict__ status) {
-  constexpr int F = Fields1<SYS>::F;
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
   __shared__ double sh[32];
   const long long n = 2 * g.plane;
   double mx = 0.0;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
-    const double* us = u + (long long)mesh * F * 3 * g.plane + cell;
-    if (SYS == SYS_EULER) {
-      const double rho = us[0], m = us[3 * g.plane], E = us[6 * g.plane];
-      const double v = m / rho;
-      const double p = (g.gamma - 1.0) * (E - 0.5 * m * v);
-      if (rho > 0.0 && p > 0.0) mx = fmax(mx, fabs(v) + sqrt(g.gamma * p / rho));
-      else atomicOr(status, ST_NONPHYSICAL);
-    } else {
-      mx = fabs(g.adv_x);
-    }
+    const double* us = u + (long long)mesh * F * M * g.plane + cell;
+    double w[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) w[f] = us[(f * M) * g.plane];
+    const double s = speed1<SYS>(g, w);
+    if (s >= 0.0) mx = fmax(mx, s);
+    else atomicOr(status, ST_NONPHYSICAL);
   }
   mx = block_reduce_max(mx, sh);
   if (threadIdx.x == 0) {
@@ -253,84 +334,99 @@ __global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict
   }
 }
 
+// Sampling points of the initial projection: K+1 Gauss points on each half of
+// every cell of both meshes, layout [mesh][i][s][q].
+template <int K>
 __global__ void k_points1d(Geo g, double ax, double* __restrict__ x) {
-  const long long n = 2 * g.plane * 6;
+  constexpr int N = K + 1, R = 2 * N;
+  const long long n = 2 * g.plane * R;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t % 6);
-    const long long c = t / 6;
+    const int r = (int)(t % R);
+    const long long c = t / R;
     const int mesh = (int)(c / g.plane);
     const long long i = c - mesh * g.plane;
     const double xc = ax + (i + 0.5 + 0.5 * mesh) * g.hx;
-    x[t] = xc + 0.5 * g.hx * xs_self(r / 3, r % 3);
+    x[t] = xc + 0.5 * g.hx * xs1(N, r / N, r % N);
   }
 }
 
-template <int F>
+// L2 projection onto P^K from values at the points of k_points1d:
+// u_a = (2a+1)/2 sum_{s,q} (w_q / 2) u0(x_sq) P_a(xi_sq).
+template <int F, int K>
 __global__ void k_project1d(Geo g, const double* __restrict__ vals, double* __restrict__ u) {
+  constexpr int M = K + 1, N = K + 1, R = 2 * N;
   const long long n = 2 * g.plane;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
-    double acc[F][3];
+    double acc[F][M];
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc[f][0] = acc[f][1] = acc[f][2] = 0.0;
-    const double* v = vals + c * 6 * F;
+    for (int f = 0; f < F; ++f)
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
-      const double xi = xs_self(r / 3, r % 3), w = 0.5 * gwt(r % 3);
+      for (int a = 0; a < M; ++a) acc[f][a] = 0.0;
+    const double* v = vals + c * R * F;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double xi = xs1(N, r / N, r % N), w = 0.5 * gw1(N, r % N);
 #pragma unroll
       for (int f = 0; f < F; ++f) {
         const double x = w * v[r * F + f];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) acc[f][a] = fma(x, lp(a, xi), acc[f][a]);
+        for (int a = 0; a < M; ++a) acc[f][a] = fma(x, lpd(a, 0, xi), acc[f][a]);
       }
     }
-    double* o = u + (long long)mesh * F * 3 * g.plane + cell;
+    double* o = u + (long long)mesh * F * M * g.plane + cell;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) o[(f * 3 + a) * g.plane] = acc[f][a] * ((2 * a + 1) / 2.0);
+      for (int a = 0; a < M; ++a) o[(f * M + a) * g.plane] = acc[f][a] * ((2 * a + 1) / 2.0);
   }
 }
 
 // ----------------------------------------------------------------- launch --
 
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// fn(IC<SYS>, IC<BC>, IC<K>) for the runtime (sys, bc, k); k in {1, 2, 3}
+template <class Fn>
+static void by_sys_bc_k(int sys, int bc, int k, Fn&& fn) {
+  auto kk = [&](auto S, auto B) {
+    if (k == 1) fn(S, B, IC<1>{});
+    else if (k == 2) fn(S, B, IC<2>{});
+    else fn(S, B, IC<3>{});
+  };
+  auto bb = [&](auto S) {
+    if (bc == BC_PERIODIC) kk(S, IC<BC_PERIODIC>{});
+    else kk(S, IC<BC_TRANSMISSIVE>{});
+  };
+  if (sys == SYS_EULER) bb(IC<SYS_EULER>{});
+  else if (sys == SYS_BURGERS) bb(IC<SYS_BURGERS>{});
+  else bb(IC<SYS_ADV>{});
+}
+
 long long partial_blocks_1d(const Geo& g) { return (g.nx + NT1 - 1) / NT1; }
 
-template <int SYS, int BC>
-static cudaError_t stage1d_t(const Geo& g, int rhs_only, const double* uin, const double* un, double* out,
-                             const double* dt, double ca, double cb, double* partials, cudaStream_t st) {
+cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, const double* uin,
+                           const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st) {
   const dim3 grid((g.nx + NT1 - 1) / NT1, 2);
-  if (rhs_only) k_stage1d<SYS, BC, MODE1_RHS><<<grid, NT1, 0, st>>>(g, uin, un, out, dt, ca, cb, partials);
-  else k_stage1d<SYS, BC, MODE1_STAGE><<<grid, NT1, 0, st>>>(g, uin, un, out, dt, ca, cb, partials);
+  by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
+    constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
+    if (rhs_only) k_stage1d<S_, B_, K_, MODE1_RHS><<<grid, NT1, 0, st>>>(g, uin, cb, out, dt, partials);
+    else k_stage1d<S_, B_, K_, MODE1_STAGE><<<grid, NT1, 0, st>>>(g, uin, cb, out, dt, partials);
+  });
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage1d(int sys, int bc, const Geo& g, int rhs_only, const double* uin, const double* un,
-                           double* out, const double* dt, double ca, double cb, double* partials, cudaStream_t st) {
-  if (sys == SYS_EULER)
-    return bc == BC_PERIODIC ? stage1d_t<SYS_EULER, BC_PERIODIC>(g, rhs_only, uin, un, out, dt, ca, cb, partials, st)
-                             : stage1d_t<SYS_EULER, BC_TRANSMISSIVE>(g, rhs_only, uin, un, out, dt, ca, cb, partials, st);
-  return bc == BC_PERIODIC ? stage1d_t<SYS_ADV, BC_PERIODIC>(g, rhs_only, uin, un, out, dt, ca, cb, partials, st)
-                           : stage1d_t<SYS_ADV, BC_TRANSMISSIVE>(g, rhs_only, uin, un, out, dt, ca, cb, partials, st);
-}
-
-template <int SYS, int BC>
-static cudaError_t oe1d_t(const Geo& g, const double* uh, double* usig, const double* dt, const double* sigma,
-                          double* delta, int* status, cudaStream_t st) {
-  const dim3 grid((g.nx + NT1 - 1) / NT1, 2);
-  if (delta) k_oe1d<SYS, BC, true><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
-  else k_oe1d<SYS, BC, false><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_oe1d(int sys, int bc, const Geo& g, const double* uh, double* usig, const double* dt,
+cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
                         const double* sigma, double* delta, int* status, cudaStream_t st) {
-  if (sys == SYS_EULER)
-    return bc == BC_PERIODIC ? oe1d_t<SYS_EULER, BC_PERIODIC>(g, uh, usig, dt, sigma, delta, status, st)
-                             : oe1d_t<SYS_EULER, BC_TRANSMISSIVE>(g, uh, usig, dt, sigma, delta, status, st);
-  return bc == BC_PERIODIC ? oe1d_t<SYS_ADV, BC_PERIODIC>(g, uh, usig, dt, sigma, delta, status, st)
-                           : oe1d_t<SYS_ADV, BC_TRANSMISSIVE>(g, uh, usig, dt, sigma, delta, status, st);
+  const dim3 grid((g.nx + NT1 - 1) / NT1, 2);
+  by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
+    constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
+    if (delta) k_oe1d<S_, B_, K_, true><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+    else k_oe1d<S_, B_, K_, false><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+  });
+  return cudaGetLastError();
 }
 
 int wave_blocks_1d(const Geo& g) {
@@ -338,23 +434,28 @@ int wave_blocks_1d(const Geo& g) {
   return (int)(b < 1184 ? b : 1184);
 }
 
-cudaError_t launch_dt1d(int sys, const Geo& g, const double* u, double* partial, int nblk, double T_end, double* dt,
-                        double* time, int* status, cudaStream_t st) {
-  if (sys == SYS_EULER) k_wave1d<SYS_EULER><<<nblk, 256, 0, st>>>(g, u, partial, status);
-  else k_wave1d<SYS_ADV><<<nblk, 256, 0, st>>>(g, u, partial, status);
+cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* partial, int nblk, double T_end,
+                        double* dt, double* time, int* status, cudaStream_t st) {
+  by_sys_bc_k(sys, BC_PERIODIC, k, [&](auto S, auto, auto Kc) {
+    k_wave1d<decltype(S)::value, decltype(Kc)::value><<<nblk, 256, 0, st>>>(g, u, partial, status);
+  });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_dt_final(partial, nblk, g.hx, g.hy, 1, g.cfl, T_end, dt, time, st);
 }
 
-cudaError_t launch_points1d(const Geo& g, double ax, double* x, cudaStream_t st) {
-  k_points1d<<<256, 256, 0, st>>>(g, ax, x);
+cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st) {
+  if (k == 1) k_points1d<1><<<256, 256, 0, st>>>(g, ax, x);
+  else if (k == 2) k_points1d<2><<<256, 256, 0, st>>>(g, ax, x);
+  else k_points1d<3><<<256, 256, 0, st>>>(g, ax, x);
   return cudaGetLastError();
 }
 
-cudaError_t launch_project1d(int sys, const Geo& g, const double* vals, double* u, cudaStream_t st) {
-  if (sys == SYS_EULER) k_project1d<3><<<256, 128, 0, st>>>(g, vals, u);
-  else k_project1d<1><<<256, 128, 0, st>>>(g, vals, u);
+cudaError_t launch_project1d(int sys, int k, const Geo& g, const double* vals, double* u, cudaStream_t st) {
+  by_sys_bc_k(sys, BC_PERIODIC, k, [&](auto S, auto, auto Kc) {
+    constexpr int F = Fields1<decltype(S)::value>::F;
+    k_project1d<F, decltype(Kc)::value><<<256, 128, 0, st>>>(g, vals, u);
+  });
   return cudaGetLastError();
 }
 

@@ -305,7 +305,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     const double rho = __ldg(us), mx = __ldg(us + 9 * P), my = __ldg(us + 18 * P), E = __ldg(us + 27 * P);
     const double r = 1.0 / rho;
     const double vx = mx * r, vy = my * r;
-    const double p = (g.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
+    const double p = (g.gamma - 1.0) * fma(-0.5, fma(mx, vx, my * vy), E);
     double c = 0.0;
     if (rho > 0.0 && p > 0.0) {
       c = sqrt(g.gamma * p * r);
@@ -424,18 +424,19 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
       }
     }
     if (sg != 0.0) {
+      // explicit fma: the recording and the plain instantiation must round alike
       const double is = 1.0 / sg;
+      const double v0 = fma(bx * cx0, Sx0, (by * cy0) * Sy0) * is;
+      const double v1 = fma(bx * cx1, Sx1, (by * cy1) * Sy1) * is;
+      const double v2 = fma(bx * cx2, Sx2, (by * cy2) * Sy2) * is;
       if (REC) {
-        const double v0 = (bx * cx0 * Sx0 + by * cy0 * Sy0) * is;
-        const double v1 = (bx * cx1 * Sx1 + by * cy1 * Sy1) * is;
-        const double v2 = (bx * cx2 * Sx2 + by * cy2 * Sy2) * is;
         if (v0 > d0) { d0 = v0; rf[0] = f; rs[0][0] = Sx0; rs[0][1] = Sy0; }
         if (v1 > d1) { d1 = v1; rf[1] = f; rs[1][0] = Sx1; rs[1][1] = Sy1; }
         if (v2 > d2) { d2 = v2; rf[2] = f; rs[2][0] = Sx2; rs[2][1] = Sy2; }
       } else {
-        d0 = fmax(d0, (bx * cx0 * Sx0 + by * cy0 * Sy0) * is);
-        d1 = fmax(d1, (bx * cx1 * Sx1 + by * cy1 * Sy1) * is);
-        d2 = fmax(d2, (bx * cx2 * Sx2 + by * cy2 * Sy2) * is);
+        d0 = fmax(d0, v0);
+        d1 = fmax(d1, v1);
+        d2 = fmax(d2, v2);
       }
     }
   }

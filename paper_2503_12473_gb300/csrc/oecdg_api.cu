@@ -62,8 +62,10 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   if (d.nx < 2 || (d.dim == 2 && d.ny < 2)) return CDG_EINVAL;
   if (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE) return CDG_EINVAL;
   if (d.system != CDG_ADVECTION && d.system != CDG_BURGERS && d.system != CDG_EULER) return CDG_EINVAL;
-  if (d.rk != CDG_RK_EULER1 && d.rk != CDG_RK_SSP3) return CDG_EUNSUPPORTED;
-  if (d.k != 2 || d.system == CDG_BURGERS || (d.dim == 2 && d.basis != CDG_BASIS_Q)) return CDG_EUNSUPPORTED;
+  if (d.rk < CDG_RK_EULER1 || d.rk > CDG_RK_RK4) return CDG_EINVAL;
+  if (d.dim == 2 && (d.k != 2 || d.system == CDG_BURGERS || d.basis != CDG_BASIS_Q || d.rk == CDG_RK_RK4))
+    return CDG_EUNSUPPORTED;
+  if (d.dim == 1 && (d.k < 1 || d.k > 3)) return CDG_EUNSUPPORTED;
   if (!(d.bx > d.ax) || (d.dim == 2 && !(d.by > d.ay)) || !(d.cfl > 0.0)) return CDG_EINVAL;
   if (d.system == CDG_EULER && !(d.gamma > 1.0)) return CDG_EINVAL;
   const long long ny = d.dim == 2 ? d.ny : 1;
@@ -75,7 +77,9 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   c->d.ny = (int)ny;
   c->stream = (cudaStream_t)stream;
   c->F = d.system == CDG_EULER ? d.dim + 2 : 1;
-  c->M = d.dim == 2 ? 9 : 3;
+  c->M = d.dim == 2 ? 9 : d.k + 1;
+  c->sys = d.system == CDG_EULER ? SYS_EULER : d.system == CDG_BURGERS ? SYS_BURGERS : SYS_ADV;
+  c->bc = d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
   Geo& g = c->g;
   g.nx = d.nx;
   g.ny = (int)ny;
@@ -100,6 +104,10 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   } while (0)
   ALLOC(buf_a, c->numel * sizeof(double));
   ALLOC(buf_b, c->numel * sizeof(double));
+  if (d.rk == CDG_RK_RK4) {
+    ALLOC(buf_c, c->numel * sizeof(double));
+    ALLOC(buf_d, c->numel * sizeof(double));
+  }
   ALLOC(partials, (size_t)2 * c->nblk * c->F * 3 * sizeof(double));
   ALLOC(wave_partial, (size_t)c->wave_blk * 2 * sizeof(double));
   ALLOC(dt, 2 * sizeof(double));
@@ -128,6 +136,8 @@ cdg_status cdg_free(cdg_ctx* c) {
   cudaStreamSynchronize(c->stream);
   cudaFree(c->buf_a);
   cudaFree(c->buf_b);
+  cudaFree(c->buf_c);
+  cudaFree(c->buf_d);
   cudaFree(c->partials);
   cudaFree(c->wave_partial);
   cudaFree(c->dt);
@@ -158,51 +168,79 @@ cdg_status cdg_launch_count(const cdg_ctx* c, long long* n) {
 
 cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts) {
   if (!ctx || !npts) return CDG_EINVAL;
-  const size_t per = ctx->d.dim == 2 ? 36 : 6;
+  const size_t per = ctx->d.dim == 2 ? 36 : 2 * (ctx->d.k + 1);
   *npts = (size_t)2 * ctx->g.plane * per;
   if (!d_xy) return CDG_OK;
   if (ctx->d.dim == 2) CK(launch_points2d(ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
-  else CK(launch_points1d(ctx->g, ctx->d.ax, d_xy, ctx->stream), "quad_points");
+  else CK(launch_points1d(ctx->d.k, ctx->g, ctx->d.ax, d_xy, ctx->stream), "quad_points");
   ctx->launches += 1;
   return CDG_OK;
 }
 
 cdg_status cdg_project_ic(cdg_ctx* ctx, const double* d_vals, double* d_u) {
   if (!ctx || !d_vals || !d_u) return fail(ctx, CDG_EINVAL, "project_ic: null pointer");
-  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
-  if (ctx->d.dim == 2) CK(launch_project2d(sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
-  else CK(launch_project1d(sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  if (ctx->d.dim == 2) CK(launch_project2d(ctx->sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  else CK(launch_project1d(ctx->sys, ctx->d.k, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
   ctx->launches += 1;
   return CDG_OK;
 }
 
-static cudaError_t run_stage(cdg_ctx* ctx, int rhs_only, const double* uin, const double* un, double* out,
-                             const double* dt, double ca, double cb) {
-  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
-  const int bc = ctx->d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
-  ctx->launches += 1;
-  prof_mark(ctx, PROF_STAGE, 0);
+// One stage kernel: out = sum_m cb.c[m] cb.u[m] + cb.ct tau L(uin) (rhs_only:
+// out = L(uin)).  The 2D kernel takes the two-state form
+// ca un + cb (uin + tau L(uin)); other forms are refused there.
+static cudaError_t run_stage(cdg_ctx* ctx, int rhs_only, const double* uin, const StageComb& cb, double* out,
+                             const double* dt) {
   cudaError_t e;
-  if (ctx->d.dim == 2)
-    e = launch_stage2d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
-  else
-    e = launch_stage1d(sys, bc, ctx->g, rhs_only, uin, un, out, dt, ca, cb, ctx->partials, ctx->stream);
+  if (ctx->d.dim == 2) {
+    const double* un = nullptr;
+    double ca = 0.0, cw = 1.0;
+    if (cb.n == 2 && cb.u[1] == uin && cb.c[1] == cb.ct) {
+      un = cb.u[0];
+      ca = cb.c[0];
+      cw = cb.ct;
+    } else if (!(cb.n == 1 && cb.u[0] == uin && cb.c[0] == 1.0 && cb.ct == 1.0)) {
+      return cudaErrorNotSupported;
+    }
+    ctx->launches += 1;
+    prof_mark(ctx, PROF_STAGE, 0);
+    e = launch_stage2d(ctx->sys, ctx->bc, ctx->g, rhs_only, uin, un, out, dt, ca, cw, ctx->partials, ctx->stream);
+  } else {
+    ctx->launches += 1;
+    prof_mark(ctx, PROF_STAGE, 0);
+    e = launch_stage1d(ctx->sys, ctx->bc, ctx->d.k, ctx->g, rhs_only, uin, cb, out, dt, ctx->partials, ctx->stream);
+  }
   prof_mark(ctx, PROF_STAGE, 1);
   return e;
 }
 
+static StageComb comb1(const double* u0, double c0, double ct) {
+  StageComb cb{};
+  cb.u[0] = u0;
+  cb.c[0] = c0;
+  cb.n = 1;
+  cb.ct = ct;
+  return cb;
+}
+
+static StageComb comb2(const double* u0, double c0, const double* u1, double c1, double ct) {
+  StageComb cb = comb1(u0, c0, ct);
+  cb.u[1] = u1;
+  cb.c[1] = c1;
+  cb.n = 2;
+  return cb;
+}
+
 // sigma from the partials of the last stage kernel, then the OE kernel
 static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* delta) {
-  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
-  const int bc = ctx->d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
   cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
   prof_mark(ctx, PROF_OE, 0);
   if (ctx->d.dim == 2)
-    e = launch_oe2d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+    e = launch_oe2d(ctx->sys, ctx->bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
   else
-    e = launch_oe1d(sys, bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
+    e = launch_oe1d(ctx->sys, ctx->bc, ctx->d.k, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status,
+                    ctx->stream);
   prof_mark(ctx, PROF_OE, 1);
   return e;
 }
@@ -213,17 +251,16 @@ cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L)
   if (!(tau_max > 0.0)) return fail(ctx, CDG_EINVAL, "rhs: tau_max must be > 0");
   CK(launch_set2(ctx->rhs_dt, 0.0, tau_max, ctx->stream), "rhs");
   ctx->launches += 1;
-  CK(run_stage(ctx, 1, d_u, nullptr, d_L, ctx->rhs_dt, 0.0, 1.0), "rhs");
+  CK(run_stage(ctx, 1, d_u, comb1(d_u, 1.0, 1.0), d_L, ctx->rhs_dt), "rhs");
   return CDG_OK;
 }
 
 static cudaError_t launch_dt(cdg_ctx* ctx, const double* d_u, double T_end) {
-  const int sys = ctx->d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
   ctx->launches += 2;
   if (ctx->d.dim == 2)
-    return launch_dt2d(sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
+    return launch_dt2d(ctx->sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
                        ctx->stream);
-  return launch_dt1d(sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
+  return launch_dt1d(ctx->sys, ctx->d.k, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
                      ctx->stream);
 }
 
@@ -260,17 +297,63 @@ cdg_status cdg_get_time(cdg_ctx* ctx, double* t) {
   return CDG_OK;
 }
 
-// SSP-RK3 (Shu-Osher) stage coefficients: out = c_l un + (1 - c_l)(ul + tau L(ul))
-static const double SSP3_C[3] = {0.0, 0.75, 1.0 / 3.0};
+static int n_stages(int rk) { return rk == CDG_RK_RK4 ? 4 : rk; }
+
+// Shu-Osher form of the context's RK method (Eq. (eq:RKCDG) with SSP-RK2/3;
+// classical RK4 for the 1D convergence study of Table 2).  U[0] = u^n, U[l] =
+// the OE-damped stage l; stage l evaluates L at U[l].
+static StageComb rk_comb(int rk, int l, const double* const* U) {
+  if (rk == CDG_RK_SSP2) return l == 0 ? comb1(U[0], 1.0, 1.0) : comb2(U[0], 0.5, U[1], 0.5, 0.5);
+  if (rk == CDG_RK_SSP3) {
+    // c_l un + (1 - c_l)(...), c = (0, 3/4, 1/3), the weights written as 1 - c_l
+    // so that every SSP-RK3 driver (single, batched, adjoint) rounds alike
+    if (l == 0) return comb1(U[0], 1.0, 1.0);
+    const double c = l == 1 ? 0.75 : 1.0 / 3.0;
+    return comb2(U[0], c, U[l], 1.0 - c, 1.0 - c);
+  }
+  if (rk == CDG_RK_RK4) {
+    if (l < 3) return comb1(U[0], 1.0, l == 2 ? 1.0 : 0.5);
+    StageComb cb = comb2(U[0], -1.0 / 3.0, U[1], 1.0 / 3.0, 1.0 / 6.0);
+    cb.u[2] = U[2];
+    cb.c[2] = 2.0 / 3.0;
+    cb.u[3] = U[3];
+    cb.c[3] = 1.0 / 3.0;
+    cb.n = 4;
+    return cb;
+  }
+  return comb1(U[0], 1.0, 1.0);
+}
 
 cdg_status cdg_rk_stage(cdg_ctx* ctx, int l, const double* d_un, const double* d_ul, double* d_out) {
   if (!ctx || !d_ul || !d_out) return fail(ctx, CDG_EINVAL, "rk_stage: null pointer");
-  const int nst = ctx->d.rk == CDG_RK_SSP3 ? 3 : 1;
+  const int rk = ctx->d.rk, nst = n_stages(rk);
   if (l < 0 || l >= nst) return fail(ctx, CDG_EINVAL, "rk_stage: stage index out of range");
+  if (rk == CDG_RK_RK4 && l == 3) return fail(ctx, CDG_EINVAL, "rk_stage: RK4's last stage needs cdg_rk_combine");
   if (l > 0 && !d_un) return fail(ctx, CDG_EINVAL, "rk_stage: d_un is null");
   if (d_out == d_ul || (l > 0 && d_out == d_un)) return fail(ctx, CDG_EINVAL, "rk_stage: output aliases an input");
-  const double ca = nst == 3 ? SSP3_C[l] : 0.0;
-  CK(run_stage(ctx, 0, d_ul, d_un, d_out, ctx->dt, ca, 1.0 - ca), "rk_stage");
+  const double* U[4] = {l == 0 ? d_ul : d_un, d_ul, d_ul, d_ul};
+  CK(run_stage(ctx, 0, d_ul, rk_comb(rk, l, U), d_out, ctx->dt), "rk_stage");
+  return CDG_OK;
+}
+
+cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double* const* d_terms, const double* coef,
+                          double ct, double* d_out) {
+  if (!ctx || !d_ul || !d_out || !d_terms || !coef) return fail(ctx, CDG_EINVAL, "rk_combine: null pointer");
+  if (n < 1 || n > 4) return fail(ctx, CDG_EINVAL, "rk_combine: n must be 1..4");
+  if (d_out == d_ul) return fail(ctx, CDG_EINVAL, "rk_combine: output aliases d_ul");
+  StageComb cb{};
+  for (int m = 0; m < n; ++m) {
+    if (!d_terms[m]) return fail(ctx, CDG_EINVAL, "rk_combine: null term");
+    if (d_terms[m] == d_out) return fail(ctx, CDG_EINVAL, "rk_combine: output aliases a term");
+    cb.u[m] = d_terms[m];
+    cb.c[m] = coef[m];
+  }
+  cb.n = n;
+  cb.ct = ct;
+  cudaError_t e = run_stage(ctx, 0, d_ul, cb, d_out, ctx->dt);
+  if (e == cudaErrorNotSupported)
+    return fail(ctx, CDG_EUNSUPPORTED, "rk_combine: the 2D stage kernel takes only the two-state form");
+  CK(e, "rk_combine");
   return CDG_OK;
 }
 
@@ -282,7 +365,7 @@ cdg_status cdg_oe_damp(cdg_ctx* ctx, const double* d_uh, double* d_usig) {
   // the cdg_step path, where the partials come from the stage that made u_h)
   CK(launch_set2(ctx->rhs_dt, 0.0, 1.0, ctx->stream), "oe_damp");
   ctx->launches += 1;
-  CK(run_stage(ctx, 0, d_uh, nullptr, ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt, 0.0, 1.0),
+  CK(run_stage(ctx, 0, d_uh, comb1(d_uh, 1.0, 1.0), ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt),
      "oe_damp");
   if (ctx->d.k == 0) return CDG_OK;
   CK(run_oe(ctx, d_uh, d_usig, nullptr), "oe_damp");
@@ -293,7 +376,7 @@ cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta
   if (!ctx || !d_uh) return fail(ctx, CDG_EINVAL, "oe_coefficients: null pointer");
   CK(launch_set2(ctx->rhs_dt, 0.0, 1.0, ctx->stream), "oe_coefficients");
   ctx->launches += 1;
-  CK(run_stage(ctx, 0, d_uh, nullptr, ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt, 0.0, 1.0),
+  CK(run_stage(ctx, 0, d_uh, comb1(d_uh, 1.0, 1.0), ctx->buf_a == d_uh ? ctx->buf_b : ctx->buf_a, ctx->rhs_dt),
      "oe_coefficients");
   if (d_delta) CK(run_oe(ctx, d_uh, nullptr, d_delta), "oe_coefficients");
   else {
@@ -311,18 +394,20 @@ cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta
 cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
   if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "step: null pointer");
   if (nsteps < 0) return fail(ctx, CDG_EINVAL, "step: nsteps < 0");
-  if (d_u == ctx->buf_a || d_u == ctx->buf_b) return fail(ctx, CDG_EINVAL, "step: d_u is a context buffer");
+  if (d_u == ctx->buf_a || d_u == ctx->buf_b || d_u == ctx->buf_c || d_u == ctx->buf_d)
+    return fail(ctx, CDG_EINVAL, "step: d_u is a context buffer");
   CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step");
   ctx->launches += 1;
-  const int nst = ctx->d.rk == CDG_RK_SSP3 ? 3 : 1;
+  const int rk = ctx->d.rk, nst = n_stages(rk);
+  // U[l]: the damped stage values.  u_h of every stage -> buf_a; u_sigma ->
+  // buf_b (RK4: stages 1..3 -> buf_b, buf_c, buf_d), the last one back into d_u.
+  const double* U[4] = {d_u, ctx->buf_b, rk == CDG_RK_RK4 ? ctx->buf_c : ctx->buf_b,
+                        rk == CDG_RK_RK4 ? ctx->buf_d : ctx->buf_b};
   for (int s = 0; s < nsteps; ++s) {
     CK(launch_dt(ctx, d_u, T_end), "step: dt");
-    // u_h^{(l+1)} -> buf_a, u_sigma^{(l+1)} -> buf_b (last stage: back into d_u)
     for (int l = 0; l < nst; ++l) {
-      const double ca = nst == 3 ? SSP3_C[l] : 0.0;
-      const double* uin = l == 0 ? d_u : ctx->buf_b;
-      CK(run_stage(ctx, 0, uin, d_u, ctx->buf_a, ctx->dt, ca, 1.0 - ca), "step: stage");
-      double* dst = (l == nst - 1) ? d_u : ctx->buf_b;
+      CK(run_stage(ctx, 0, U[l], rk_comb(rk, l, U), ctx->buf_a, ctx->dt), "step: stage");
+      double* dst = (l == nst - 1) ? d_u : (double*)U[l + 1];
       if (ctx->d.oe) {
         CK(run_oe(ctx, ctx->buf_a, dst, nullptr), "step: oe");
       } else {

@@ -19,6 +19,10 @@ struct cdg_ctx {
   int wave_blk;          // blocks of the wave-speed reduction
   double* buf_a;         // scratch state (u_h)
   double* buf_b;         // scratch state (u_sigma)
+  double* buf_c;         // RK4 only: u^(2)
+  double* buf_d;         // RK4 only: u^(3)
+  int sys;               // SYS_ADV / SYS_BURGERS / SYS_EULER
+  int bc;                // BC_PERIODIC / BC_TRANSMISSIVE
   double* partials;      // [2][nblk][F][3]
   double* wave_partial;  // [wave_blk][2]
   double* dt;            // [tau, tau_max]

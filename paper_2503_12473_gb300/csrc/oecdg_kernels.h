@@ -17,17 +17,25 @@ cudaError_t launch_dt2d(int sys, const Geo& g, const double* u, double* partial,
 cudaError_t launch_points2d(const Geo& g, double ax, double ay, double* xy, cudaStream_t st);
 cudaError_t launch_project2d(int sys, const Geo& g, const double* vals, double* u, cudaStream_t st);
 
-// 1D P^2
+// One Shu-Osher stage: out = sum_{m < n} c[m] u[m] + ct tau L(u_l).
+struct StageComb {
+  const double* u[4];
+  double c[4];
+  int n;
+  double ct;
+};
+
+// 1D P^k, k in {1, 2, 3}
 long long partial_blocks_1d(const Geo& g);
 int wave_blocks_1d(const Geo& g);
-cudaError_t launch_stage1d(int sys, int bc, const Geo& g, int rhs_only, const double* uin, const double* un,
-                           double* out, const double* dt, double ca, double cb, double* partials, cudaStream_t st);
-cudaError_t launch_oe1d(int sys, int bc, const Geo& g, const double* uh, double* usig, const double* dt,
+cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, const double* uin,
+                           const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st);
+cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
                         const double* sigma, double* delta, int* status, cudaStream_t st);
-cudaError_t launch_dt1d(int sys, const Geo& g, const double* u, double* partial, int nblk, double T_end, double* dt,
-                        double* time, int* status, cudaStream_t st);
-cudaError_t launch_points1d(const Geo& g, double ax, double* x, cudaStream_t st);
-cudaError_t launch_project1d(int sys, const Geo& g, const double* vals, double* u, cudaStream_t st);
+cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* partial, int nblk, double T_end,
+                        double* dt, double* time, int* status, cudaStream_t st);
+cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st);
+cudaError_t launch_project1d(int sys, int k, const Geo& g, const double* vals, double* u, cudaStream_t st);
 
 // shared
 cudaError_t launch_sigma(const double* partials, long long nblk, int F, long long ncell, double* sigma, double* avg,

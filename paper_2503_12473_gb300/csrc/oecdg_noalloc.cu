@@ -154,6 +154,6 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
   if (cudaGetLastError() != cudaSuccess) return CDG_ECUDA;
   if (launch_sigma(partials, nblk, F, cells, sigma, avg, st) != cudaSuccess) return CDG_ECUDA;
   cudaError_t e = d.dim == 2 ? launch_oe2d(sys, bc, g, d_uh, d_usig, dt, sigma, nullptr, status, st)
-                             : launch_oe1d(sys, bc, g, d_uh, d_usig, dt, sigma, nullptr, status, st);
+                             : launch_oe1d(sys, bc, 2, g, d_uh, d_usig, dt, sigma, nullptr, status, st);
   return e == cudaSuccess ? CDG_OK : CDG_ECUDA;
 }

@@ -19,7 +19,7 @@ CDG_OK, CDG_EINVAL, CDG_ENOMEM, CDG_ECUDA, CDG_ENONPHYSICAL, CDG_ETIMEOUT, CDG_E
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
-RK_EULER1, RK_SSP3 = 1, 3
+RK_EULER1, RK_SSP2, RK_SSP3, RK_RK4 = 1, 2, 3, 4
 
 STATUS_NAMES = {0: "CDG_OK", 1: "CDG_EINVAL", 2: "CDG_ENOMEM", 3: "CDG_ECUDA", 4: "CDG_ENONPHYSICAL",
                 5: "CDG_ETIMEOUT", 6: "CDG_EUNSUPPORTED"}
@@ -32,6 +32,7 @@ EXPORTED = [
     "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
     "cdg_step_adjoint", "cdg_batch_set_rows", "cdg_record_numel", "cdg_step_record", "cdg_step_adjoint_recorded",
+    "cdg_rk_combine",
 ]
 
 
@@ -94,6 +95,9 @@ def load(build_if_missing: bool = True):
     L.cdg_get_dt.argtypes = [vp, dp, dp]
     L.cdg_rk_stage.restype = st
     L.cdg_rk_stage.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    L.cdg_rk_combine.restype = st
+    L.cdg_rk_combine.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, vp]
     L.cdg_oe_damp.restype = st
     L.cdg_oe_damp.argtypes = [vp, vp, vp]
     L.cdg_oe_coefficients.restype = st
@@ -190,7 +194,7 @@ class MeshDesc:
 
     @property
     def nmodes(self) -> int:
-        return 9 if self.dim == 2 else 3
+        return 9 if self.dim == 2 else self.k + 1
 
     @property
     def shape(self):
@@ -282,6 +286,12 @@ class Context:
 
     def cdg_rk_stage(self, l: int, d_un, d_ul, d_out):
         self._ck(self._L.cdg_rk_stage(self.h, l, _ptr(d_un), _ptr(d_ul), _ptr(d_out)), "cdg_rk_stage")
+
+    def cdg_rk_combine(self, d_ul, terms, coefs, ct: float, d_out):
+        n = len(terms)
+        tp = (ctypes.c_void_p * max(n, 1))(*[_ptr(t) for t in terms])
+        cp = (ctypes.c_double * max(n, 1))(*[float(c) for c in coefs])
+        self._ck(self._L.cdg_rk_combine(self.h, _ptr(d_ul), n, tp, cp, float(ct), _ptr(d_out)), "cdg_rk_combine")
 
     def cdg_oe_damp(self, d_uh, d_usig):
         self._ck(self._L.cdg_oe_damp(self.h, _ptr(d_uh), _ptr(d_usig)), "cdg_oe_damp")

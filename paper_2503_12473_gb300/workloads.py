@@ -11,6 +11,9 @@ Workloads (sizes and data):
   * ``shu_osher_1d``  -- 1D Euler, gamma = 1.4, [-5, 5] transmissive, 4000 cells,
     (rho, v, p) = (3.857143, 2.629369, 10.33333) for x < -4, else
     (1 + 0.2 sin 5x, 0, 1) (the Shu-Osher data of Section 4), T = 1.8.
+  * ``burgers_1d``    -- u_t + (u^2/2)_x = 0, u0 = sin x + 0.5 on [0, 2pi] periodic,
+    P^3, classical RK4, CFL 0.31, T = 0.6 (the Table 2 accuracy test).
+  * ``euler_wave_1d`` -- 1D Euler density wave (1 + 0.2 sin x, 1, 1), periodic.
   * ``riemann_2d``    -- 2D Euler four-quadrant Riemann data split at (0.8, 0.8) on
     [0,1]^2 transmissive, 1024^2, Q^2, CFL 0.1, 200 steps.
   * ``batched_2d``    -- 256 periodic 2D Euler problems with seeded sizes and data.
@@ -100,6 +103,22 @@ def sine_1d(period: float = 2.0 * math.pi, a: float = 0.0):
     def f(xy):
         x = np.asarray(xy, dtype=np.float64).reshape(len(xy), -1)[:, 0]
         return np.sin(2.0 * math.pi * (x - a) / period)[:, None]
+    return f
+
+
+def burgers_sine(offset: float = 0.5):
+    """u0 = sin x + offset (the Burgers accuracy test of Table 2)."""
+    def f(xy):
+        x = np.asarray(xy, dtype=np.float64).reshape(len(xy), -1)[:, 0]
+        return (np.sin(x) + offset)[:, None]
+    return f
+
+
+def density_wave_1d(gamma=GAMMA, amp: float = 0.2):
+    """Smooth 1D Euler data (rho, v, p) = (1 + amp sin x, 1, 1), 2 pi periodic."""
+    def f(xy):
+        x = np.asarray(xy, dtype=np.float64).reshape(len(xy), -1)[:, 0]
+        return prim_to_cons_1d(1.0 + amp * np.sin(x), np.ones_like(x), np.ones_like(x), gamma)
     return f
 
 
@@ -261,6 +280,16 @@ def advection_1d(n: int = 128) -> Workload:
 def shu_osher_1d(n: int = 4000) -> Workload:
     return Workload("euler_1d_shu_osher_p2_4000", 1, n, 1, 2, EULER, TRANSMISSIVE, -5.0, 5.0, cfl=0.1, T=1.8,
                     u0=shu_osher())
+
+
+def burgers_1d(n: int = 128, k: int = 3) -> Workload:
+    return Workload(f"burgers_1d_p{k}_{n}", 1, n, 1, k, BURGERS, PERIODIC, 0.0, 2.0 * math.pi, cfl=0.31, rk=4,
+                    T=0.6, u0=burgers_sine(0.5))
+
+
+def euler_wave_1d(n: int = 128, k: int = 2) -> Workload:
+    return Workload(f"euler_1d_wave_p{k}_{n}", 1, n, 1, k, EULER, PERIODIC, 0.0, 2.0 * math.pi, cfl=0.1,
+                    T=0.5, u0=density_wave_1d())
 
 
 def riemann_2d(n: int = 1024, steps: int = 200) -> Workload:
