@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboecdg.so")
-SOURCES = ["oecdg_api.cu", "oecdg_2d.cu", "oecdg_1d.cu", "oecdg_noalloc.cu", "oecdg_batch.cu", "oecdg_adjoint.cu"]
+SOURCES = ["oecdg_api.cu", "oecdg_2d.cu", "oecdg_1d.cu", "oecdg_noalloc.cu", "oecdg_batch.cu", "oecdg_adjoint.cu", "oecdg_2dk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -9,42 +9,12 @@
 
 #include "oecdg_common.cuh"
 #include "oecdg_kernels.h"
+#include "oecdg_poly.cuh"
 
 namespace oecdg {
 
 constexpr int NT1 = 128;
 constexpr double DINF1 = __builtin_huge_val();
-
-// (K+1)-point Gauss-Legendre rules on [-1, 1], nodes in increasing order:
-//  2 points: +-1/sqrt(3), weights 1;
-//  3 points: 0, +-sqrt(3/5), weights 8/9, 5/9;
-//  4 points: +-sqrt(3/7 -+ (2/7) sqrt(6/5)), weights (18 +- sqrt(30)) / 36.
-__host__ __device__ constexpr double gn1(int N, int q) {
-  return N == 2 ? (q == 0 ? -0.57735026918962576451 : 0.57735026918962576451)
-       : N == 3 ? gnode(q)
-       : (q == 0 ? -0.86113631159405257522
-          : q == 1 ? -0.33998104358485626480 : q == 2 ? 0.33998104358485626480 : 0.86113631159405257522);
-}
-__host__ __device__ constexpr double gw1(int N, int q) {
-  return N == 2 ? 1.0
-       : N == 3 ? gwt(q)
-       : ((q == 0 || q == 3) ? 0.34785484513745385737 : 0.65214515486254614263);
-}
-
-// d-th derivative of the unnormalised Legendre polynomial P_n (n <= 3)
-__host__ __device__ constexpr double lpd(int n, int d, double x) {
-  return d == 0 ? (n == 0 ? 1.0 : n == 1 ? x : n == 2 ? 1.5 * x * x - 0.5 : (2.5 * x * x - 1.5) * x)
-       : d == 1 ? (n == 0 ? 0.0 : n == 1 ? 1.0 : n == 2 ? 3.0 * x : 7.5 * x * x - 1.5)
-       : d == 2 ? (n < 2 ? 0.0 : n == 2 ? 3.0 : 15.0 * x)
-       : d == 3 ? (n == 3 ? 15.0 : 0.0)
-       : 0.0;
-}
-__host__ __device__ constexpr double fact(int m) { return m <= 1 ? 1.0 : m * fact(m - 1); }
-
-// points of half s in the cell's own reference coordinate and in the
-// overlapping cell (N-point rule)
-__host__ __device__ constexpr double xs1(int N, int s, int q) { return s - 0.5 + 0.5 * gn1(N, q); }
-__host__ __device__ constexpr double xo1(int N, int s, int q) { return 0.5 - s + 0.5 * gn1(N, q); }
 
 template <int SYS>
 struct Fields1 {

@@ -1136,8 +1136,8 @@ static cudaError_t adj_backward(cdg_ctx* c, const double* un, const double* cons
 }
 
 static cdg_status adj_check(cdg_ctx* ctx) {
-  if (ctx->d.dim != 2 || ctx->d.bc != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
-    return adj_fail(ctx, CDG_EUNSUPPORTED, "adjoint: 2D periodic SSP-RK3 only");
+  if (ctx->d.dim != 2 || ctx->gen2 || ctx->d.bc != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
+    return adj_fail(ctx, CDG_EUNSUPPORTED, "adjoint: 2D periodic Q^2 SSP-RK3 only");
   cdg_status s = adj_alloc(ctx);
   if (s != CDG_OK) return adj_fail(ctx, s, "adjoint: allocation failed");
   return CDG_OK;

@@ -36,6 +36,8 @@ static void prof_release(cdg_ctx* c) {
   c->prof_on = 0;
 }
 
+static int basis_of(const cdg_ctx* c) { return c->d.basis == CDG_BASIS_Q ? BASIS_Q : BASIS_P; }
+
 static cdg_status fail(cdg_ctx* c, cdg_status s, const char* msg) {
   if (c) snprintf(c->err, sizeof c->err, "%s", msg);
   return s;
@@ -63,9 +65,8 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   if (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE) return CDG_EINVAL;
   if (d.system != CDG_ADVECTION && d.system != CDG_BURGERS && d.system != CDG_EULER) return CDG_EINVAL;
   if (d.rk < CDG_RK_EULER1 || d.rk > CDG_RK_RK4) return CDG_EINVAL;
-  if (d.dim == 2 && (d.k != 2 || d.system == CDG_BURGERS || d.basis != CDG_BASIS_Q || d.rk == CDG_RK_RK4))
-    return CDG_EUNSUPPORTED;
-  if (d.dim == 1 && (d.k < 1 || d.k > 3)) return CDG_EUNSUPPORTED;
+  if (d.basis != CDG_BASIS_Q && d.basis != CDG_BASIS_P) return CDG_EINVAL;
+  if (d.k < 1 || d.k > 3) return CDG_EUNSUPPORTED;
   if (!(d.bx > d.ax) || (d.dim == 2 && !(d.by > d.ay)) || !(d.cfl > 0.0)) return CDG_EINVAL;
   if (d.system == CDG_EULER && !(d.gamma > 1.0)) return CDG_EINVAL;
   const long long ny = d.dim == 2 ? d.ny : 1;
@@ -77,7 +78,10 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   c->d.ny = (int)ny;
   c->stream = (cudaStream_t)stream;
   c->F = d.system == CDG_EULER ? d.dim + 2 : 1;
-  c->M = d.dim == 2 ? 9 : d.k + 1;
+  // the tiled kernels serve Q^2 with forward Euler / SSP-RK2 / SSP-RK3 for
+  // advection and Euler; every other 2D configuration runs the generic ones
+  c->gen2 = d.dim == 2 && (d.k != 2 || d.basis != CDG_BASIS_Q || d.system == CDG_BURGERS || d.rk == CDG_RK_RK4);
+  c->M = d.dim == 2 ? modes_2k(d.k, d.basis == CDG_BASIS_Q ? BASIS_Q : BASIS_P) : d.k + 1;
   c->sys = d.system == CDG_EULER ? SYS_EULER : d.system == CDG_BURGERS ? SYS_BURGERS : SYS_ADV;
   c->bc = d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
   Geo& g = c->g;
@@ -91,7 +95,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   g.adv_y = d.adv_y;
   g.cfl = d.cfl;
   c->numel = (size_t)2 * c->F * c->M * g.plane;
-  c->nblk = d.dim == 2 ? partial_blocks_2d(g) : partial_blocks_1d(g);
+  c->nblk = d.dim == 2 ? (c->gen2 ? partial_blocks_2k(g) : partial_blocks_2d(g)) : partial_blocks_1d(g);
   c->wave_blk = d.dim == 2 ? wave_blocks_2d(g) : wave_blocks_1d(g);
 
   cudaError_t e = cudaSuccess;
@@ -168,10 +172,12 @@ cdg_status cdg_launch_count(const cdg_ctx* c, long long* n) {
 
 cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts) {
   if (!ctx || !npts) return CDG_EINVAL;
-  const size_t per = ctx->d.dim == 2 ? 36 : 2 * (ctx->d.k + 1);
+  const size_t q = ctx->d.k + 1;
+  const size_t per = ctx->d.dim == 2 ? 4 * q * q : 2 * q;
   *npts = (size_t)2 * ctx->g.plane * per;
   if (!d_xy) return CDG_OK;
-  if (ctx->d.dim == 2) CK(launch_points2d(ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
+  if (ctx->gen2) CK(launch_points2k(ctx->d.k, ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
+  else if (ctx->d.dim == 2) CK(launch_points2d(ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
   else CK(launch_points1d(ctx->d.k, ctx->g, ctx->d.ax, d_xy, ctx->stream), "quad_points");
   ctx->launches += 1;
   return CDG_OK;
@@ -179,7 +185,8 @@ cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts) {
 
 cdg_status cdg_project_ic(cdg_ctx* ctx, const double* d_vals, double* d_u) {
   if (!ctx || !d_vals || !d_u) return fail(ctx, CDG_EINVAL, "project_ic: null pointer");
-  if (ctx->d.dim == 2) CK(launch_project2d(ctx->sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  if (ctx->gen2) CK(launch_project2k(ctx->sys, ctx->d.k, basis_of(ctx), ctx->g, d_vals, d_u, ctx->stream), "project_ic");
+  else if (ctx->d.dim == 2) CK(launch_project2d(ctx->sys, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
   else CK(launch_project1d(ctx->sys, ctx->d.k, ctx->g, d_vals, d_u, ctx->stream), "project_ic");
   ctx->launches += 1;
   return CDG_OK;
@@ -191,7 +198,12 @@ cdg_status cdg_project_ic(cdg_ctx* ctx, const double* d_vals, double* d_u) {
 static cudaError_t run_stage(cdg_ctx* ctx, int rhs_only, const double* uin, const StageComb& cb, double* out,
                              const double* dt) {
   cudaError_t e;
-  if (ctx->d.dim == 2) {
+  if (ctx->gen2) {
+    ctx->launches += 1;
+    prof_mark(ctx, PROF_STAGE, 0);
+    e = launch_stage2k(ctx->sys, ctx->bc, ctx->d.k, basis_of(ctx), ctx->g, rhs_only, uin, cb, out, dt, ctx->partials,
+                       ctx->stream);
+  } else if (ctx->d.dim == 2) {
     const double* un = nullptr;
     double ca = 0.0, cw = 1.0;
     if (cb.n == 2 && cb.u[1] == uin && cb.c[1] == cb.ct) {
@@ -236,7 +248,10 @@ static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* 
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
   prof_mark(ctx, PROF_OE, 0);
-  if (ctx->d.dim == 2)
+  if (ctx->gen2)
+    e = launch_oe2k(ctx->sys, ctx->bc, ctx->d.k, basis_of(ctx), ctx->g, uh, usig, ctx->dt, ctx->sigma, delta,
+                    ctx->status, ctx->stream);
+  else if (ctx->d.dim == 2)
     e = launch_oe2d(ctx->sys, ctx->bc, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status, ctx->stream);
   else
     e = launch_oe1d(ctx->sys, ctx->bc, ctx->d.k, ctx->g, uh, usig, ctx->dt, ctx->sigma, delta, ctx->status,
@@ -257,6 +272,9 @@ cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L)
 
 static cudaError_t launch_dt(cdg_ctx* ctx, const double* d_u, double T_end) {
   ctx->launches += 2;
+  if (ctx->gen2)
+    return launch_dt2k(ctx->sys, ctx->d.k, basis_of(ctx), ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end,
+                       ctx->dt, ctx->time, ctx->status, ctx->stream);
   if (ctx->d.dim == 2)
     return launch_dt2d(ctx->sys, ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end, ctx->dt, ctx->time, ctx->status,
                        ctx->stream);
@@ -352,7 +370,7 @@ cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double*
   cb.ct = ct;
   cudaError_t e = run_stage(ctx, 0, d_ul, cb, d_out, ctx->dt);
   if (e == cudaErrorNotSupported)
-    return fail(ctx, CDG_EUNSUPPORTED, "rk_combine: the 2D stage kernel takes only the two-state form");
+    return fail(ctx, CDG_EUNSUPPORTED, "rk_combine: the tiled Q^2 stage kernel takes only the two-state form");
   CK(e, "rk_combine");
   return CDG_OK;
 }

@@ -10,6 +10,7 @@ namespace oecdg {
 
 enum { SYS_ADV = 0, SYS_BURGERS = 1, SYS_EULER = 2 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+enum { BASIS_Q = 0, BASIS_P = 1 };
 
 // status bits written by kernels
 enum { ST_NONPHYSICAL = 1 };

@@ -23,6 +23,7 @@ struct cdg_ctx {
   double* buf_d;         // RK4 only: u^(3)
   int sys;               // SYS_ADV / SYS_BURGERS / SYS_EULER
   int bc;                // BC_PERIODIC / BC_TRANSMISSIVE
+  int gen2;              // 2D configuration served by the degree-generic kernels
   double* partials;      // [2][nblk][F][3]
   double* wave_partial;  // [wave_blk][2]
   double* dt;            // [tau, tau_max]

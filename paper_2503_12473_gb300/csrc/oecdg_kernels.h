@@ -37,6 +37,19 @@ cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* p
 cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st);
 cudaError_t launch_project1d(int sys, int k, const Geo& g, const double* vals, double* u, cudaStream_t st);
 
+// 2D Q^k / P^k, k in {1, 2, 3}: every configuration outside the tiled Q^2 path
+long long partial_blocks_2k(const Geo& g);
+int modes_2k(int k, int basis);
+cudaError_t launch_stage2k(int sys, int bc, int k, int basis, const Geo& g, int rhs_only, const double* uin,
+                           const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st);
+cudaError_t launch_oe2k(int sys, int bc, int k, int basis, const Geo& g, const double* uh, double* usig,
+                        const double* dt, const double* sigma, double* delta, int* status, cudaStream_t st);
+cudaError_t launch_dt2k(int sys, int k, int basis, const Geo& g, const double* u, double* partial, int nblk,
+                        double T_end, double* dt, double* time, int* status, cudaStream_t st);
+cudaError_t launch_points2k(int k, const Geo& g, double ax, double ay, double* xy, cudaStream_t st);
+cudaError_t launch_project2k(int sys, int k, int basis, const Geo& g, const double* vals, double* u,
+                             cudaStream_t st);
+
 // shared
 cudaError_t launch_sigma(const double* partials, long long nblk, int F, long long ncell, double* sigma, double* avg,
                          cudaStream_t st);

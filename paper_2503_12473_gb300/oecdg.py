@@ -194,7 +194,9 @@ class MeshDesc:
 
     @property
     def nmodes(self) -> int:
-        return 9 if self.dim == 2 else self.k + 1
+        if self.dim == 1:
+            return self.k + 1
+        return (self.k + 1) ** 2 if self.basis == BASIS_Q else (self.k + 1) * (self.k + 2) // 2
 
     @property
     def shape(self):

@@ -225,8 +225,8 @@ def test_scope_checks():
     from paper_2503_12473_gb300 import oecdg as G
     for kw, status in ((dict(dim=1, nx=16, k=4), G.CDG_EUNSUPPORTED),
                        (dict(dim=1, nx=16, k=0), G.CDG_EUNSUPPORTED),
-                       (dict(dim=2, nx=8, ny=8, rk=4), G.CDG_EUNSUPPORTED),
-                       (dict(dim=2, nx=8, ny=8, system=G.BURGERS), G.CDG_EUNSUPPORTED),
+                       (dict(dim=2, nx=8, ny=8, k=4), G.CDG_EUNSUPPORTED),
+                       (dict(dim=2, nx=8, ny=8, basis=7), G.CDG_EINVAL),
                        (dict(dim=1, nx=16, rk=5), G.CDG_EINVAL)):
         with pytest.raises(G.CdgError) as e:
             G.Context(G.MeshDesc(**kw))

@@ -241,7 +241,7 @@ def test_invalid_arguments():
         G.Context(G.MeshDesc(dim=2, nx=1, ny=8))
     assert e.value.status == G.CDG_EINVAL
     with pytest.raises(G.CdgError) as e:
-        G.Context(G.MeshDesc(dim=2, nx=8, ny=8, k=3))
+        G.Context(G.MeshDesc(dim=2, nx=8, ny=8, k=4))
     assert e.value.status == G.CDG_EUNSUPPORTED
     ctx = G.Context(G.MeshDesc(dim=2, nx=8, ny=8))
     u = ctx.zeros()
