@@ -50,7 +50,7 @@ HBM_FALLBACK_GBS = 6800.0
 FLOPS_PER_CELL = {"stage": 7472, "oe": 7418}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
 # once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 859, "oe": 809}
+TRAFFIC_PER_CELL = {"stage": 855, "oe": 809}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
 # (neighbour re-reads are L2 hits).
@@ -138,7 +138,9 @@ def job_value(dof: int, steps: int, ws: int, ms_max: float) -> float:
 def config_dict(n, dof):
     return {"workload": f"euler_2d_riemann_q2_{n}", "model": None, "nx": n, "ny": n, "k": 2, "basis": "Q",
             "system": "euler", "bc": "transmissive", "rk": "ssp-rk3", "cfl": 0.1, "oe": True, "dof": dof,
-            "l2": "inputs larger than L2 (state 604 MB > 129 MB L2)", "parallelism": "replicas"}
+            "l2": (f"inputs larger than L2 (state {dof * 8 / 1e6:.0f} MB > 129 MB L2)" if dof * 8 > 129e6 else
+                   f"state {dof * 8 / 1e6:.0f} MB fits in L2: not a bench configuration"),
+            "parallelism": "replicas"}
 
 
 # ---------------------------------------------------------------- oracle ---
