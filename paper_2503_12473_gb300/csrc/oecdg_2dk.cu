@@ -121,6 +121,11 @@ __device__ __forceinline__ void eval_fields(const double* __restrict__ c, long l
 //         - (2/hx) sum_{x-faces} (w_q/2) s f1 phi_m - (2/hy) sum_{y-faces} (w_q/2) s f2 phi_m,
 // s = -1 / +1 the face side.  (The u_K part of the dissipation term is exact:
 // int_K u_K phi_m = u_m ||phi_m||^2.)
+// Sum factorisation by rows of points: for each row qy of a sub-cell the
+// overlapping cell is contracted in y once (T), each point then costs K+1
+// terms per field, and the x sums of the row (X: value and d/dx terms, Y: d/dy
+// term) are projected in y once.  Face rows likewise: the overlapping cell at
+// its centre line (Z), the face sums per tangential degree (G), one projection.
 template <int SYS, int BC, int K, int B>
 __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restrict__ u, int mesh, int i, int j,
                                            double inv_tm, double (&L)[Fields2<SYS>::F][Modes2<K, B>::M]) {
@@ -139,54 +144,125 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
     const int sx = sub & 1, sy = sub >> 1;
     const int oi = wrap_index<BC>(i + sx + off, g.nx), oj = wrap_index<BC>(j + sy + off, g.ny);
     const double* c = uo + (long long)oj * g.nx + oi;
-    // volume and dissipation terms on sub-cell (sx, sy)
+    // ---- volume and dissipation terms on sub-cell (sx, sy), row by row
 #pragma unroll 1
-    for (int q = 0; q < N * N; ++q) {
-      const int qx = q % N, qy = q / N;
-      const double gx = GNK[N - 2][qx], gy = GNK[N - 2][qy];
-      const double W = 0.25 * GWK[N - 2][qx] * GWK[N - 2][qy];
-      double V[F], f1[F], f2[F];
-      eval_fields<F, K, B>(c, P, 0.5 - sx + 0.5 * gx, 0.5 - sy + 0.5 * gy, V);
-      flux2<SYS>(g, V, f1, f2);
-      double px[K + 1], py[K + 1], dx[K + 1], dy[K + 1];
-      leg_row<K, 0>(sx - 0.5 + 0.5 * gx, px);
-      leg_row<K, 0>(sy - 0.5 + 0.5 * gy, py);
-      leg_row<K, 1>(sx - 0.5 + 0.5 * gx, dx);
-      leg_row<K, 1>(sy - 0.5 + 0.5 * gy, dy);
+    for (int qy = 0; qy < N; ++qy) {
+      const double gy = GNK[N - 2][qy], wy = GWK[N - 2][qy];
+      double T[F][K + 1];  // overlapping cell contracted in y at this row
+      {
+        double pyo[K + 1];
+        leg_row<K, 0>(0.5 - sy + 0.5 * gy, pyo);
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        const double a1 = W * sx2 * f1[f], a2 = W * sy2 * f2[f], av = W * inv_tm * V[f];
+        for (int f = 0; f < F; ++f) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          double r = fma(px[MD::a(m)] * py[MD::b(m)], av, L[f][m]);
-          if (MD::a(m) > 0) r = fma(dx[MD::a(m)] * py[MD::b(m)], a1, r);
-          if (MD::b(m) > 0) r = fma(px[MD::a(m)] * dy[MD::b(m)], a2, r);
-          L[f][m] = r;
+          for (int a = 0; a <= K; ++a) T[f][a] = 0.0;
+#pragma unroll
+          for (int m = 0; m < M; ++m)
+            T[f][MD::a(m)] = fma(pyo[MD::b(m)], __ldg(c + (f * M + m) * P), T[f][MD::a(m)]);
         }
       }
-    }
-    // x-face on side sx, half sy (K's xi = 2 sx - 1, overlapping xi' = 0) and
-    // y-face on side sy, half sx (K's eta = 2 sy - 1, overlapping eta' = 0)
+      double X[F][K + 1], Y[F][K + 1];
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int a = 0; a <= K; ++a) X[f][a] = Y[f][a] = 0.0;
 #pragma unroll 1
-    for (int q = 0; q < 2 * N; ++q) {
-      const int dir = q / N, qq = q % N;
-      const double gq = GNK[N - 2][qq], wq = GWK[N - 2][qq];
+      for (int qx = 0; qx < N; ++qx) {
+        const double gx = GNK[N - 2][qx];
+        const double W = 0.25 * GWK[N - 2][qx] * wy;
+        double pxo[K + 1], px[K + 1], dpx[K + 1];
+        leg_row<K, 0>(0.5 - sx + 0.5 * gx, pxo);
+        leg_row<K, 0>(sx - 0.5 + 0.5 * gx, px);
+        leg_row<K, 1>(sx - 0.5 + 0.5 * gx, dpx);
+        double V[F], f1[F], f2[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          double v = 0.0;
+#pragma unroll
+          for (int a = 0; a <= K; ++a) v = fma(pxo[a], T[f][a], v);
+          V[f] = v;
+        }
+        flux2<SYS>(g, V, f1, f2);
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          const double av = W * inv_tm * V[f], a1 = W * sx2 * f1[f], a2 = W * sy2 * f2[f];
+#pragma unroll
+          for (int a = 0; a <= K; ++a) {
+            X[f][a] = fma(px[a], av, a > 0 ? fma(dpx[a], a1, X[f][a]) : X[f][a]);
+            Y[f][a] = fma(px[a], a2, Y[f][a]);
+          }
+        }
+      }
+      double py[K + 1], dpy[K + 1];
+      leg_row<K, 0>(sy - 0.5 + 0.5 * gy, py);
+      leg_row<K, 1>(sy - 0.5 + 0.5 * gy, dpy);
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double r = fma(py[MD::b(m)], X[f][MD::a(m)], L[f][m]);
+          if (MD::b(m) > 0) r = fma(dpy[MD::b(m)], Y[f][MD::a(m)], r);
+          L[f][m] = r;
+        }
+    }
+    // ---- x-face on side sx, half sy (K's xi = 2 sx - 1, overlapping xi' = 0)
+    //      y-face on side sy, half sx (K's eta = 2 sy - 1, overlapping eta' = 0)
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
       const int h = dir == 0 ? sy : sx;
       const double sgn = dir == 0 ? 2.0 * sx - 1.0 : 2.0 * sy - 1.0;
-      const double t = h - 0.5 + 0.5 * gq, to = 0.5 - h + 0.5 * gq;
-      double V[F], f1[F], f2[F];
-      eval_fields<F, K, B>(c, P, dir == 0 ? 0.0 : to, dir == 0 ? to : 0.0, V);
-      flux2<SYS>(g, V, f1, f2);
-      double px[K + 1], py[K + 1];
-      leg_row<K, 0>(dir == 0 ? sgn : t, px);
-      leg_row<K, 0>(dir == 0 ? t : sgn, py);
-      const double sc = -0.5 * wq * sgn * (dir == 0 ? sx2 : sy2);
+      double Z[F][K + 1];  // overlapping cell on its centre line, by tangential degree
+      {
+        double p0[K + 1];
+        leg_row<K, 0>(0.0, p0);
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        const double cf = sc * (dir == 0 ? f1[f] : f2[f]);
+        for (int f = 0; f < F; ++f) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) L[f][m] = fma(px[MD::a(m)] * py[MD::b(m)], cf, L[f][m]);
+          for (int a = 0; a <= K; ++a) Z[f][a] = 0.0;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const int an = dir == 0 ? MD::a(m) : MD::b(m), at = dir == 0 ? MD::b(m) : MD::a(m);
+            Z[f][at] = fma(p0[an], __ldg(c + (f * M + m) * P), Z[f][at]);
+          }
+        }
       }
+      double Gs[F][K + 1];  // sum over the points of the face weight x P_at(t)
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int a = 0; a <= K; ++a) Gs[f][a] = 0.0;
+      const double sc = -0.5 * sgn * (dir == 0 ? sx2 : sy2);
+#pragma unroll 1
+      for (int q = 0; q < N; ++q) {
+        const double gq = GNK[N - 2][q], wq = GWK[N - 2][q];
+        double pto[K + 1], pt[K + 1];
+        leg_row<K, 0>(0.5 - h + 0.5 * gq, pto);
+        leg_row<K, 0>(h - 0.5 + 0.5 * gq, pt);
+        double V[F], f1[F], f2[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          double v = 0.0;
+#pragma unroll
+          for (int a = 0; a <= K; ++a) v = fma(pto[a], Z[f][a], v);
+          V[f] = v;
+        }
+        flux2<SYS>(g, V, f1, f2);
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          const double cf = sc * wq * (dir == 0 ? f1[f] : f2[f]);
+#pragma unroll
+          for (int a = 0; a <= K; ++a) Gs[f][a] = fma(pt[a], cf, Gs[f][a]);
+        }
+      }
+      double pn[K + 1];
+      leg_row<K, 0>(sgn, pn);
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int an = dir == 0 ? MD::a(m) : MD::b(m), at = dir == 0 ? MD::b(m) : MD::a(m);
+          L[f][m] = fma(pn[an], Gs[f][at], L[f][m]);
+        }
     }
   }
   const double* us = u + (long long)mesh * F * M * P + (long long)j * g.nx + i;
@@ -324,43 +400,87 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
     for (int n = 0; n < 2; ++n) {
       const double sn = n == 0 ? 2.0 / g.hx : 2.0 / g.hy, st = n == 0 ? 2.0 / g.hy : 2.0 / g.hx;
 #pragma unroll 1
-      for (int hs = 0; hs < 4; ++hs) {
-        const int side = hs & 1, h = hs >> 1;
-        const int oi = wrap_index<BC>(i + (n == 0 ? side : h) + off, g.nx);
-        const int oj = wrap_index<BC>(j + (n == 0 ? h : side) + off, g.ny);
-        const double* co = uo + (long long)(f * M) * P + (long long)oj * g.nx + oi;
-        double cw[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) cw[m] = __ldg(co + (long long)m * P);
+      for (int side = 0; side < 2; ++side) {
         const double s = 2.0 * side - 1.0;
+        // K's trace series on the face: Tu[an][at] = coefficient of P_at(t) in
+        // the an-th normal derivative (reference) at normal coordinate s
+        double Tu[K + 1][K + 1];
+        {
+          double pn[K + 1][K + 1];  // pn[d][a] = P_a^(d)(s)
+#pragma unroll
+          for (int d = 0; d <= K; ++d)
+#pragma unroll
+            for (int a = 0; a <= K; ++a) pn[d][a] = lpd(a, d, s);
+#pragma unroll
+          for (int d = 0; d <= K; ++d)
+#pragma unroll
+            for (int a = 0; a <= K; ++a) Tu[d][a] = 0.0;
+#pragma unroll
+          for (int mm = 0; mm < M; ++mm) {
+            const int a_n = n == 0 ? MD::a(mm) : MD::b(mm), a_t = n == 0 ? MD::b(mm) : MD::a(mm);
+#pragma unroll
+            for (int d = 0; d <= a_n; ++d) Tu[d][a_t] = fma(pn[d][a_n], cu[mm], Tu[d][a_t]);
+          }
+        }
 #pragma unroll 1
-        for (int q = 0; q < N; ++q) {
-          const double gq = GNK[N - 2][q], wq = GWK[N - 2][q];
-          const double t = h - 0.5 + 0.5 * gq, to = 0.5 - h + 0.5 * gq;
+        for (int h = 0; h < 2; ++h) {
+          const int oi = wrap_index<BC>(i + (n == 0 ? side : h) + off, g.nx);
+          const int oj = wrap_index<BC>(j + (n == 0 ? h : side) + off, g.ny);
+          const double* co = uo + (long long)(f * M) * P + (long long)oj * g.nx + oi;
+          // the overlapping cell's series on its centre line (normal coordinate 0)
+          double Tw[K + 1][K + 1];
 #pragma unroll
-          for (int m = 0; m <= K; ++m) {
-            double ss = 0.0;
+          for (int d = 0; d <= K; ++d)
 #pragma unroll
-            for (int an = 0; an <= m; ++an) {
-              const int at = m - an;
-              // scale sn^an st^at
-              double sc = 1.0;
+            for (int a = 0; a <= K; ++a) Tw[d][a] = 0.0;
 #pragma unroll
-              for (int r = 0; r < an; ++r) sc *= sn;
+          for (int mm = 0; mm < M; ++mm) {
+            const int a_n = n == 0 ? MD::a(mm) : MD::b(mm), a_t = n == 0 ? MD::b(mm) : MD::a(mm);
+            const double cw = __ldg(co + (long long)mm * P);
 #pragma unroll
-              for (int r = 0; r < at; ++r) sc *= st;
-              double dv = 0.0;
+            for (int d = 0; d <= a_n; ++d)
+              if (lpd(a_n, d, 0.0) != 0.0) Tw[d][a_t] = fma(lpd(a_n, d, 0.0), cw, Tw[d][a_t]);
+          }
+          // difference series in K's tangential coordinate t (t' = t + dl):
+          // E[an] = Tu[an] - Tw[an] re-expanded about t
+          const double dl = 1.0 - 2.0 * h;
+          double E[K + 1][K + 1];
 #pragma unroll
-              for (int mm = 0; mm < M; ++mm) {
-                const int a_n = n == 0 ? MD::a(mm) : MD::b(mm), a_t = n == 0 ? MD::b(mm) : MD::a(mm);
-                if (a_n < an || a_t < at) continue;
-                dv = fma(lpd(a_n, an, s) * lpd(a_t, at, t), cu[mm], dv);
-                dv = fma(-lpd(a_n, an, 0.0) * lpd(a_t, at, to), cw[mm], dv);
-              }
-              dv *= sc;
-              ss = fma(dv, dv, ss);
+          for (int d = 0; d <= K; ++d)
+#pragma unroll
+            for (int a = 0; a <= K; ++a) {
+              double e = Tu[d][a];
+#pragma unroll
+              for (int a2 = a; a2 <= K; ++a2)
+                if (!(B == BASIS_P && a2 + d > K)) e = fma(-lshift(a2, a, dl), Tw[d][a2], e);
+              E[d][a] = e;
             }
-            S[n][m] = fma(wq, sqrt(ss), S[n][m]);
+#pragma unroll 1
+          for (int q = 0; q < N; ++q) {
+            const double gq = GNK[N - 2][q], wq = GWK[N - 2][q];
+            const double t = h - 0.5 + 0.5 * gq;
+#pragma unroll
+            for (int m = 0; m <= K; ++m) {
+              double ss = 0.0;
+#pragma unroll
+              for (int an = 0; an <= m; ++an) {
+                const int at = m - an;
+                double v = 0.0;
+#pragma unroll
+                for (int a = at; a <= K; ++a) {
+                  if (B == BASIS_P && a + an > K) continue;  // no such mode in P^K
+                  v = fma(E[an][a], lpd(a, at, t), v);
+                }
+                double sc = 1.0;
+#pragma unroll
+                for (int r = 0; r < an; ++r) sc *= sn;
+#pragma unroll
+                for (int r = 0; r < at; ++r) sc *= st;
+                const double dv = v * sc;
+                ss = fma(dv, dv, ss);
+              }
+              S[n][m] = fma(wq, sqrt(ss), S[n][m]);
+            }
           }
         }
       }

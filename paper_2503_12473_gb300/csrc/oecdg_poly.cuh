@@ -33,6 +33,17 @@ __host__ __device__ constexpr double lpd(int n, int d, double x) {
        : d == 3 ? (n == 3 ? 15.0 : 0.0)
        : 0.0;
 }
+// Coefficient of P_to(t) in P_from(t + d) for d = +1 or -1 (re-expansion of a
+// Legendre series under a shift by a whole reference half-width):
+//   P_1(t+d) = P_1 + d,  P_2(t+d) = P_2 + 3d P_1 + 3/2,
+//   P_3(t+d) = P_3 + 5d P_2 + 15/2 P_1 + 7/2 d.
+__host__ __device__ constexpr double lshift(int from, int to, double d) {
+  return from == to ? 1.0
+       : from == 1 ? (to == 0 ? d : 0.0)
+       : from == 2 ? (to == 1 ? 3.0 * d : to == 0 ? 1.5 : 0.0)
+       : from == 3 ? (to == 2 ? 5.0 * d : to == 1 ? 7.5 : to == 0 ? 3.5 * d : 0.0)
+       : 0.0;
+}
 __host__ __device__ constexpr double fact(int m) { return m <= 1 ? 1.0 : m * fact(m - 1); }
 
 // Points of half (sub-cell) s in the cell's own reference coordinate and the
