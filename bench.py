@@ -313,6 +313,92 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# Executed FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes per cell of the
+# degree-generic 2D kernels, 2D Euler, periodic, one 512^2 launch each (the
+# state is larger than L2 for k >= 2); keys (k, basis).  Source:
+# profiles/fp64_counts_euler2d_generic.md.
+FLOPS_PER_CELL_2K = {(1, "P"): {"stage": 3409, "oe": 3091}, (2, "P"): {"stage": 9731, "oe": 8011},
+                     (3, "P"): {"stage": 22207, "oe": 17222}, (1, "Q"): {"stage": 3399, "oe": 3699},
+                     (3, "Q"): {"stage": 25070, "oe": 24750}}
+# None where the 512^2 state fits in L2 (k = 1, and P^2 at 100 MB): DRAM bytes
+# of that capture would not scale to a larger launch.
+TRAFFIC_PER_CELL_2K = {(3, "P"): {"stage": 1119, "oe": 952}, (3, "Q"): {"stage": 1495, "oe": 1498}}
+
+
+def run_generic(args, ws, rank, local):
+    """2D Euler steady wave (the smooth test of Table 4): Q^k or P^k, k = 1..3,
+    with the (k+1)-order RK method of the accuracy tests, on the degree-generic
+    kernels; DOF-updates per second per RK stage and the roofline of the
+    dominant kernel."""
+    import torch
+    from paper_2503_12473_gb300 import oecdg as G
+    from paper_2503_12473_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    G.load()
+    k, basis = args.k, (W.BASIS_P if args.basis == "P" else W.BASIS_Q)
+    n = args.n
+    w = W.steady_wave_2d_workload(n, k, basis)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w), stream=stream)
+    dof = ctx.cdg_state_numel()
+    stages = 4 if w.rk == 4 else w.rk
+    with torch.cuda.stream(stream):
+        u = ctx.project(w.u0)
+        ctx.cdg_step_async(u, 0.0, 0.0, args.warmup)
+        stream.synchronize()
+        if ctx.cdg_check_status() != G.CDG_OK:
+            raise RuntimeError("warm-up reached a non-physical state")
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        launches0 = ctx.cdg_launch_count()
+        ctx.cdg_profile_begin(stages * args.steps + 8)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.cdg_step_async(u, 0.0, 0.0, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks_res = clocks.stop()
+        prof = ctx.cdg_profile_end()
+        launches = ctx.cdg_launch_count() - launches0
+        ms = ev0.elapsed_time(ev1)
+        if ctx.cdg_check_status() != G.CDG_OK:
+            raise RuntimeError("timed steps reached a non-physical state")
+    if rank != 0:
+        return
+    cells = 2 * n * n
+    kname = "stage" if prof["stage"][0] >= prof["oe"][0] else "oe"
+    kms, kcount = prof[kname]
+    avg_s = (kms / max(kcount, 1)) * 1e-3
+    key = (k, args.basis)
+    fpc = FLOPS_PER_CELL_2K.get(key, {}).get(kname)
+    tpc = TRAFFIC_PER_CELL_2K.get(key, {}).get(kname)
+    if k == 2 and args.basis == "Q" and w.rk != 4:
+        fpc, tpc = FLOPS_PER_CELL[kname], None
+    tiled = k == 2 and args.basis == "Q" and w.rk != 4  # served by the tiled Q^2 kernels
+    roof = {"bound": "alu", "kernel": f"k_{kname}{'2d' if tiled else '2k'} (Euler, periodic, {args.basis}{k})",
+            "unit": "TFLOP/s",
+            "peak": FP64_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+            "avg_launch_ms": avg_s * 1e3, "launches": kcount,
+            "achieved": fpc * cells / avg_s / 1e12 if fpc else None,
+            "frac": fpc * cells / avg_s / 1e12 / FP64_PEAK_TFLOPS if fpc else None,
+            "flops_per_cell": fpc, "traffic": tpc * cells if tpc else None, "traffic_unit": "bytes per launch",
+            "kernel_share": {q: prof[q][0] / ms for q in ("stage", "oe")}}
+    line = {"metric": METRIC.replace("2D Euler 1024^2 k=2", f"2D Euler steady wave {n}^2 {args.basis}{k}"),
+            "value": dof * stages * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "nx": n, "ny": n, "k": k, "basis": args.basis, "system": "euler",
+                       "bc": "periodic", "rk": {2: "ssp-rk2", 3: "ssp-rk3", 4: "rk4"}[w.rk], "cfl": w.cfl,
+                       "oe": True, "dof": dof,
+                       "l2": (f"inputs larger than L2 (state {dof * 8 / 1e6:.0f} MB > 129 MB L2)"
+                              if dof * 8 > 129e6 else f"state {dof * 8 / 1e6:.0f} MB fits in L2")},
+            "roofline": roof, "gpu_launches": launches, "clocks": clocks_res}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args, ws, rank, local):
     """256 independent periodic 2D Euler Q^2 problems (seeded sizes in
     {64,...,512}^2 and data): one graph-captured batched launch per phase
@@ -460,9 +546,12 @@ def main():
     ap.add_argument("--n", type=int, default=1024, help="cells per direction (the workload is 1024)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched", "adjoint"],
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched", "adjoint", "steady-wave"],
                     help="riemann: the metric's workload (default); batched: 256 uneven meshes; "
-                         "adjoint: gradient of the vortex loss (cost and finite-difference check)")
+                         "adjoint: gradient of the vortex loss (cost and finite-difference check); "
+                         "steady-wave: the degree-generic 2D kernels on the smooth Euler test of Table 4")
+    ap.add_argument("--k", type=int, default=3, help="steady-wave: degree 1..3")
+    ap.add_argument("--basis", default="P", choices=["P", "Q"], help="steady-wave: P^k or Q^k")
     ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
@@ -476,6 +565,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload == "adjoint":
         run_adjoint(args, ws, rank, local)
+    elif args.workload == "steady-wave":
+        run_generic(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

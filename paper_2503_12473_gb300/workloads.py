@@ -292,6 +292,15 @@ def euler_wave_1d(n: int = 128, k: int = 2) -> Workload:
                     T=0.5, u0=density_wave_1d())
 
 
+def steady_wave_2d_workload(n: int = 1024, k: int = 3, basis: int = BASIS_P) -> Workload:
+    """The smooth 2D Euler test of Table 4 on [0, 2]^2, periodic, with the
+    (k+1)-order RK method and the accuracy-test CFL number of Section 4."""
+    rk = {1: 2, 2: 3, 3: 4}[k]
+    cfl = {1: 0.45, 2: 0.33, 3: 0.31}[k]
+    return Workload(f"euler_2d_steady_wave_{'QP'[basis]}{k}_{n}", 2, n, n, k, EULER, PERIODIC, 0.0, 2.0, 0.0, 2.0,
+                    basis=basis, cfl=cfl, rk=rk, T=10.0, u0=steady_wave_2d())
+
+
 def riemann_2d(n: int = 1024, steps: int = 200) -> Workload:
     return Workload("euler_2d_riemann_q2_1024", 2, n, n, 2, EULER, TRANSMISSIVE, 0.0, 1.0, 0.0, 1.0, cfl=0.1,
                     steps=steps, u0=riemann_quadrants())
