@@ -397,33 +397,53 @@ static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* 
   orc_gauss(nq, gx, gw);
   double hx = hx_of(p), hy = hy_of(p);
   int nqy = d == 2 ? nq : 1;
-  double vol = 0.0;
-  double tot[ORC_MAXF] = {0};
-  double v[ORC_MAXF];
-  /* fixed (sequential) summation order */
-  for (int j = 0; j < p->ny; ++j)
+  /* fixed summation order: each row of cells in sequence, then the rows in
+   * sequence (the rows may be summed by different threads) */
+  double* rows = (double*)calloc((size_t)p->ny * (F + 1), sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < p->ny; ++j) {
+    double v[ORC_MAXF];
+    double* r = rows + (size_t)j * (F + 1);
     for (int i = 0; i < p->nx; ++i)
       for (int qy = 0; qy < nqy; ++qy)
         for (int qx = 0; qx < nq; ++qx) {
           double W = 0.5 * gw[qx] * hx * (d == 2 ? 0.5 * gw[qy] * hy : 1.0);
           cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
-          for (int f = 0; f < F; ++f) tot[f] += W * v[f];
-          vol += W;
+          for (int f = 0; f < F; ++f) r[f] += W * v[f];
+          r[F] += W;
         }
+  }
+  double vol = 0.0;
+  double tot[ORC_MAXF] = {0};
+  for (int j = 0; j < p->ny; ++j) {
+    for (int f = 0; f < F; ++f) tot[f] += rows[(size_t)j * (F + 1) + f];
+    vol += rows[(size_t)j * (F + 1) + F];
+  }
+  free(rows);
   for (int f = 0; f < F; ++f) {
     avg[f] = tot[f] / vol;
     sig[f] = 0.0;
   }
-  for (int j = 0; j < p->ny; ++j)
-    for (int i = 0; i < p->nx; ++i)
-      for (int qy = 0; qy < nqy; ++qy)
-        for (int qx = 0; qx < nq; ++qx) {
-          cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
-          for (int f = 0; f < F; ++f) {
-            double e = fabs(v[f] - avg[f]);
-            if (e > sig[f]) sig[f] = e;
+  /* the max of |u - avg| over all points (order-independent) */
+#pragma omp parallel
+  {
+    double loc[ORC_MAXF] = {0};
+    double v[ORC_MAXF];
+#pragma omp for schedule(static)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i)
+        for (int qy = 0; qy < nqy; ++qy)
+          for (int qx = 0; qx < nq; ++qx) {
+            cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
+            for (int f = 0; f < F; ++f) {
+              double e = fabs(v[f] - avg[f]);
+              if (e > loc[f]) loc[f] = e;
+            }
           }
-        }
+#pragma omp critical
+    for (int f = 0; f < F; ++f)
+      if (loc[f] > sig[f]) sig[f] = loc[f];
+  }
 }
 
 static double factorial(int m) {
@@ -531,6 +551,62 @@ int orc_oe_coefficients(const orc_problem* p, const double* u, double* delta, do
   return status;
 }
 
+/* Decay factor of a mode of total degree deg >= 1 over the OE step of length
+ * tau (Eq. (OEstep2D) solved exactly): exp(-tau sum_{m=0}^{min(deg,k)} delta^m). */
+static double oe_factor(const orc_problem* p, const double* dl, int deg, double tau) {
+  double rate = 0.0;
+  for (int q = 0; q <= p->k && q <= deg; ++q) rate += dl[q];
+  return exp(-tau * rate);
+}
+
+/* Sampled evaluation for checks on meshes too large for a whole-mesh oracle
+ * run: the same per-cell functions as orc_rhs / orc_oe_coefficients /
+ * orc_oe_apply, applied to a list of cells only.  cells: n triples
+ * (mesh, i, j) of stored cells (j = 0 in 1D).
+ *   orc_rhs_cells: L of the listed cells, out [n][F][M].
+ *   orc_oe_cells:  sigma and avg of both meshes (whole meshes, as in
+ *                  orc_oe_coefficients; out [2][F] each, either may be NULL),
+ *                  delta of the listed cells (out [n][k+1]) and, if usig is not
+ *                  NULL, their coefficients after the OE step of length tau
+ *                  (out [n][F][M]).  Returns ORC_ENONPHYSICAL if a listed
+ *                  cell's average is not a physical state. */
+void orc_rhs_cells(const orc_problem* p, const double* u, double tau_max, int n, const int* cells, double* L) {
+  int F = nfields(p), M = nmodes(p);
+  double inv = 1.0 / tau_max;
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < n; ++c) cell_rhs(p, u, inv, cells[3 * c], cells[3 * c + 1], cells[3 * c + 2], L + (size_t)c * F * M);
+}
+
+int orc_oe_cells(const orc_problem* p, const double* u, double tau, int n, const int* cells, double* delta,
+                 double* sigma, double* avg, double* usig) {
+  int F = nfields(p), K1 = p->k + 1;
+  int ma[ORC_MAXM], mb[ORC_MAXM];
+  int M = modes(p, ma, mb);
+  double s[2][ORC_MAXF], a[2][ORC_MAXF];
+  for (int mesh = 0; mesh < 2; ++mesh) {
+    mesh_sigma(p, u, mesh, a[mesh], s[mesh]);
+    for (int f = 0; f < F; ++f) {
+      if (sigma) sigma[mesh * F + f] = s[mesh][f];
+      if (avg) avg[mesh * F + f] = a[mesh][f];
+    }
+  }
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int c = 0; c < n; ++c) {
+    int mesh = cells[3 * c], i = cells[3 * c + 1], j = cells[3 * c + 2];
+    double dl[ORC_MAXQ];
+    if (cell_delta(p, u, mesh, i, j, s[mesh], dl) != ORC_OK) bad = 1;
+    for (int m = 0; m < K1; ++m) delta[(size_t)c * K1 + m] = dl[m];
+    if (usig) {
+      for (int m = 0; m < M; ++m) {
+        double fac = m > 0 ? oe_factor(p, dl, ma[m] + mb[m], tau) : 1.0;
+        for (int f = 0; f < F; ++f) usig[((size_t)c * F + f) * M + m] = u[sidx(p, mesh, f, m, j, i)] * fac;
+      }
+    }
+  }
+  return bad ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
 /* Exact solution of the damping ODE (OEstep2D) at t_hat = tau.  In the
  * orthogonal Legendre basis, u - P^{m-1} u keeps exactly the modes of total
  * degree >= max(m, 1) (P^{-1} := P^0), so mode (a, b) obeys
@@ -544,10 +620,7 @@ void orc_oe_apply(const orc_problem* p, const double* delta, double tau, double*
       for (int i = 0; i < p->nx; ++i) {
         const double* dl = delta + (((size_t)mesh * p->ny + j) * p->nx + i) * K1;
         for (int m = 1; m < M; ++m) {
-          int deg = ma[m] + mb[m];
-          double rate = 0.0;
-          for (int q = 0; q <= p->k && q <= deg; ++q) rate += dl[q];
-          double fac = exp(-tau * rate);
+          double fac = oe_factor(p, dl, ma[m] + mb[m], tau);
           for (int f = 0; f < F; ++f) u[sidx(p, mesh, f, m, j, i)] *= fac;
         }
       }

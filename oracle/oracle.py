@@ -81,6 +81,10 @@ def lib():
         L.orc_project.argtypes = [P, dp, dp]
         L.orc_eval_cells.argtypes = [P, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
         L.orc_eval_points.argtypes = [P, dp, ctypes.c_int, ctypes.c_size_t, dp, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.orc_rhs_cells.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ip, dp]
+        L.orc_oe_cells.restype = ctypes.c_int
+        L.orc_oe_cells.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ip, dp, dp, dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib_handle = L
@@ -193,6 +197,36 @@ def oe_coefficients(p: Problem, u: np.ndarray):
     pc = p.c()
     st = lib().orc_oe_coefficients(ctypes.byref(pc), _dp(u), _dp(delta), _dp(sigma), _dp(avg))
     return delta, sigma, avg, st
+
+
+def _cells(cells) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+
+
+def rhs_cells(p: Problem, u: np.ndarray, tau_max: float, cells) -> np.ndarray:
+    """L of the listed cells ((mesh, i, j) rows): [n, F, M]."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = _cells(cells)
+    out = np.zeros((len(c), p.nfields, p.nmodes))
+    pc = p.c()
+    lib().orc_rhs_cells(ctypes.byref(pc), _dp(u), tau_max, len(c), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        _dp(out))
+    return out
+
+
+def oe_cells(p: Problem, u: np.ndarray, tau: float, cells):
+    """(delta [n, k+1], sigma [2, F], avg [2, F], damped coefficients [n, F, M],
+    status) for the listed cells, sigma and avg over the whole meshes."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    c = _cells(cells)
+    delta = np.zeros((len(c), p.k + 1))
+    sigma = np.zeros((2, p.nfields))
+    avg = np.zeros((2, p.nfields))
+    usig = np.zeros((len(c), p.nfields, p.nmodes))
+    pc = p.c()
+    st = lib().orc_oe_cells(ctypes.byref(pc), _dp(u), tau, len(c), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            _dp(delta), _dp(sigma), _dp(avg), _dp(usig))
+    return delta, sigma, avg, usig, st
 
 
 def oe_apply(p: Problem, u: np.ndarray, delta: np.ndarray, tau: float) -> np.ndarray:

@@ -535,3 +535,32 @@ def test_vortex_initial_data_is_a_translating_solution():
         fy = (flux(f(0)(pts + ey))[1] - flux(f(0)(pts - ey))[1]) / (2 * d)
         res.append(np.abs(ut + fx + fy).max())
     assert res[1] < res[0] / 3.5 and res[1] < 1e-3
+
+
+@pytest.mark.parametrize("dim,k,basis,system,bc", [(2, 2, O.BASIS_Q, O.EULER, O.TRANSMISSIVE),
+                                                   (2, 3, O.BASIS_P, O.ADVECTION, O.PERIODIC),
+                                                   (1, 3, O.BASIS_Q, O.BURGERS, O.PERIODIC)])
+def test_sampled_cells_match_whole_mesh(dim, k, basis, system, bc):
+    """The sampled entry points (used at mesh sizes where a whole-mesh oracle run
+    is too slow) give exactly the whole-mesh functions' values at the listed
+    cells: the same per-cell code, so bit-for-bit."""
+    ny = 7 if dim == 2 else 1
+    p = O.Problem(dim=dim, nx=9, ny=ny, k=k, basis=basis, system=system, bc=bc, ax=0.0, bx=1.0, ay=0.0, by=1.0)
+    rng = np.random.default_rng(3)
+    u = W.random_modal(p.shape, 11, scale=0.1)
+    if system == O.EULER:
+        u[:, 0, 0] += 1.0
+        u[:, 3, 0] += 2.5
+    cells = [(m, i, j) for m in range(2) for j in range(ny) for i in range(9) if rng.random() < 0.4]
+    L = O.rhs(p, u, 0.02)
+    Ls = O.rhs_cells(p, u, 0.02, cells)
+    d, s, a, st = O.oe_coefficients(p, u)
+    ds, ss, as_, us, st2 = O.oe_cells(p, u, 0.01, cells)
+    uo, _ = O.oe(p, u, 0.01)
+    assert st == st2
+    np.testing.assert_array_equal(ss, s)
+    np.testing.assert_array_equal(as_, a)
+    for q, (m, i, j) in enumerate(cells):
+        np.testing.assert_array_equal(Ls[q], L[m, :, :, j, i])
+        np.testing.assert_array_equal(ds[q], d[m, j, i])
+        np.testing.assert_array_equal(us[q], uo[m, :, :, j, i])
