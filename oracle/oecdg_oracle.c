@@ -51,6 +51,26 @@
 #include <omp.h>
 #endif
 
+/* State-dependent values have type `real`: double here.  The same source,
+ * compiled with ORC_COMPLEX_STEP defined (oecdg_oracle_cs.c), makes `real`
+ * double complex for complex-step differentiation: f(u + i h v) carries
+ * h J v in its imaginary part.  |x|, comparisons and max/min then act on real
+ * parts (the branch the value takes), sqrt and exp are the complex ones. */
+#ifdef ORC_COMPLEX_STEP
+#include <complex.h>
+typedef double complex real;
+#define RE(x) creal(x)
+#define R_ABS(x) (creal(x) < 0.0 ? -(x) : (x))
+#define R_SQRT(x) csqrt(x)
+#define R_EXP(x) cexp(x)
+#else
+typedef double real;
+#define RE(x) (x)
+#define R_ABS(x) fabs(x)
+#define R_SQRT(x) sqrt(x)
+#define R_EXP(x) exp(x)
+#endif
+
 #define ORC_MAXK 3
 #define ORC_MAXQ (ORC_MAXK + 1)
 #define ORC_MAXF 4
@@ -198,19 +218,19 @@ static double basis(const orc_problem* p, int a, int b, int dx, int dy, double x
 
 /* Value (dx = dy = 0) or physical derivative of every field of stored cell
  * (i, j) of mesh `mesh` at reference point (xi, eta). */
-static void cell_eval(const orc_problem* p, const double* u, int mesh, int i, int j, double xi, double eta,
-                      int dx, int dy, double* out) {
+static void cell_eval(const orc_problem* p, const real* u, int mesh, int i, int j, double xi, double eta,
+                      int dx, int dy, real* out) {
   int ma[ORC_MAXM], mb[ORC_MAXM];
   int M = modes(p, ma, mb), F = nfields(p);
   for (int f = 0; f < F; ++f) {
-    double s = 0.0;
+    real s = 0.0;
     for (int m = 0; m < M; ++m) s += u[sidx(p, mesh, f, m, j, i)] * basis(p, ma[m], mb[m], dx, dy, xi, eta);
     out[f] = s;
   }
 }
 
 /* Value of the mesh-`mesh` solution at a physical point. */
-static void point_eval(const orc_problem* p, const double* u, int mesh, double x, double y, double* out) {
+static void point_eval(const orc_problem* p, const real* u, int mesh, double x, double y, real* out) {
   int si, sj;
   double xi, eta;
   locate(p, mesh, x, y, &si, &sj, &xi, &eta);
@@ -222,7 +242,7 @@ static void point_eval(const orc_problem* p, const double* u, int mesh, double x
 /* Physical flux components f1(w), f2(w) of the conservation law. Euler:
  * Section 4, 1D and 2D Euler subsections; advection u_t + a.grad u = 0;
  * Burgers f = u^2/2 (1D). */
-static void flux(const orc_problem* p, const double* w, double* f1, double* f2) {
+static void flux(const orc_problem* p, const real* w, real* f1, real* f2) {
   if (p->system == ORC_ADVECTION) {
     f1[0] = p->adv_x * w[0];
     f2[0] = p->adv_y * w[0];
@@ -230,17 +250,17 @@ static void flux(const orc_problem* p, const double* w, double* f1, double* f2) 
     f1[0] = 0.5 * w[0] * w[0];
     f2[0] = 0.5 * w[0] * w[0];
   } else if (p->dim == 1) {
-    double rho = w[0], m = w[1], E = w[2];
-    double v = m / rho;
-    double pr = (p->gamma - 1.0) * (E - 0.5 * rho * v * v);
+    real rho = w[0], m = w[1], E = w[2];
+    real v = m / rho;
+    real pr = (p->gamma - 1.0) * (E - 0.5 * rho * v * v);
     f1[0] = m;
     f1[1] = m * v + pr;
     f1[2] = (E + pr) * v;
     f2[0] = f2[1] = f2[2] = 0.0;
   } else {
-    double rho = w[0], mx = w[1], my = w[2], E = w[3];
-    double vx = mx / rho, vy = my / rho;
-    double pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
+    real rho = w[0], mx = w[1], my = w[2], E = w[3];
+    real vx = mx / rho, vy = my / rho;
+    real pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
     f1[0] = mx;
     f1[1] = mx * vx + pr;
     f1[2] = my * vx;
@@ -255,16 +275,16 @@ static void flux(const orc_problem* p, const double* w, double* f1, double* f2) 
 /* Spectral radius of n . df/du at state w (the local wave speed beta_{e,K},
  * Section 2.2 and the Remark on systems).  Returns -1 on a non-physical Euler
  * state (rho <= 0 or p <= 0). */
-static double wave_speed(const orc_problem* p, const double* w, double nx, double ny) {
+static real wave_speed(const orc_problem* p, const real* w, double nx, double ny) {
   if (p->system == ORC_ADVECTION) return fabs(p->adv_x * nx + p->adv_y * ny);
-  if (p->system == ORC_BURGERS) return fabs(w[0] * (nx + ny));
-  double rho = w[0];
-  double vx = w[1] / rho, vy = p->dim == 2 ? w[2] / rho : 0.0;
-  double E = w[p->dim + 1];
-  double pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
-  if (!(rho > 0.0) || !(pr > 0.0)) return -1.0;
-  double c = sqrt(p->gamma * pr / rho);
-  return fabs(vx * nx + vy * ny) + c;
+  if (p->system == ORC_BURGERS) return R_ABS(w[0] * (nx + ny));
+  real rho = w[0];
+  real vx = w[1] / rho, vy = p->dim == 2 ? w[2] / rho : 0.0;
+  real E = w[p->dim + 1];
+  real pr = (p->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
+  if (!(RE(rho) > 0.0) || !(RE(pr) > 0.0)) return -1.0;
+  real c = R_SQRT(p->gamma * pr / rho);
+  return R_ABS(vx * nx + vy * ny) + c;
 }
 
 /* ------------------------------------------------------- CDG operator H --- */
@@ -277,8 +297,8 @@ static double wave_speed(const orc_problem* p, const double* w, double nx, doubl
  * points on each of the 2^d sub-cells of K cut by the overlapping mesh; face
  * integrals: (k+1) Gauss points on each of the 2 half-faces of every face (1D:
  * point faces).  Both are exact for a linear flux. */
-static void cell_rhs(const orc_problem* p, const double* u, double inv_tmax, int mesh, int i, int j,
-                     double* L /* [F][M] */) {
+static void cell_rhs(const orc_problem* p, const real* u, real inv_tmax, int mesh, int i, int j,
+                     real* L /* [F][M] */) {
   int ma[ORC_MAXM], mb[ORC_MAXM];
   int M = modes(p, ma, mb), F = nfields(p), k = p->k, nq = k + 1, d = p->dim;
   int other = 1 - mesh;
@@ -287,9 +307,9 @@ static void cell_rhs(const orc_problem* p, const double* u, double inv_tmax, int
   orc_gauss(nq, gx, gw);
   double xc, yc;
   cell_centre(p, mesh, i, j, &xc, &yc);
-  double R[ORC_MAXF][ORC_MAXM];
+  real R[ORC_MAXF][ORC_MAXM];
   memset(R, 0, sizeof R);
-  double w[ORC_MAXF], uk[ORC_MAXF], f1[ORC_MAXF], f2[ORC_MAXF];
+  real w[ORC_MAXF], uk[ORC_MAXF], f1[ORC_MAXF], f2[ORC_MAXF];
 
   /* volume and dissipation terms on the sub-cells */
   int nsy = d == 2 ? 2 : 1, nqy = d == 2 ? nq : 1;
@@ -330,7 +350,7 @@ static void cell_rhs(const orc_problem* p, const double* u, double inv_tmax, int
         for (int m = 0; m < M; ++m) {
           double ph = basis(p, ma[m], mb[m], 0, 0, xi, d == 2 ? eta : 0.0);
           for (int f = 0; f < F; ++f) {
-            double fn = dir == 0 ? side * f1[f] : side * f2[f];
+            real fn = dir == 0 ? side * f1[f] : side * f2[f];
             R[f][m] -= W * fn * ph;
           }
         }
@@ -346,14 +366,14 @@ static void cell_rhs(const orc_problem* p, const double* u, double inv_tmax, int
 }
 
 /* Semi-discrete right-hand side dU/dt = L(U) on both meshes. */
-void orc_rhs(const orc_problem* p, const double* u, double tau_max, double* L) {
+void orc_rhs(const orc_problem* p, const real* u, real tau_max, real* L) {
   int F = nfields(p), M = nmodes(p);
-  double inv = 1.0 / tau_max;
+  real inv = 1.0 / tau_max;
   for (int mesh = 0; mesh < 2; ++mesh) {
 #pragma omp parallel for collapse(2) schedule(static)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
-        double Lc[ORC_MAXF * ORC_MAXM];
+        real Lc[ORC_MAXF * ORC_MAXM];
         cell_rhs(p, u, inv, mesh, i, j, Lc);
         for (int f = 0; f < F; ++f)
           for (int m = 0; m < M; ++m) L[sidx(p, mesh, f, m, j, i)] = Lc[f * M + m];
@@ -361,6 +381,7 @@ void orc_rhs(const orc_problem* p, const double* u, double tau_max, double* L) {
   }
 }
 
+#ifndef ORC_COMPLEX_STEP
 /* Bilinear form H(u, phi) for a test function given by its modal coefficients
  * (both meshes): H(u, phi) = sum_K sum_modes R_K(u) phi_K. */
 double orc_bilinear(const orc_problem* p, const double* u, const double* phi, double tau_max) {
@@ -384,6 +405,7 @@ double orc_bilinear(const orc_problem* p, const double* u, const double* phi, do
   free(L);
   return s;
 }
+#endif
 
 /* --------------------------------------------------------- OE procedure --- */
 
@@ -391,7 +413,7 @@ double orc_bilinear(const orc_problem* p, const double* u, const double* phi, do
  *   avg(u) = (1/|Omega|) int_Omega u   (cell Gauss rule, stored cells only),
  *   sigma  = || u - avg(u) ||_{L^inf}, the max taken over the (k+1)^d Gauss
  *            points of every stored cell (parity unpinned: a convention). */
-static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* avg, double* sig) {
+static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg, real* sig) {
   int F = nfields(p), nq = p->k + 1, d = p->dim;
   double gx[ORC_MAXQ], gw[ORC_MAXQ];
   orc_gauss(nq, gx, gw);
@@ -399,11 +421,11 @@ static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* 
   int nqy = d == 2 ? nq : 1;
   /* fixed summation order: each row of cells in sequence, then the rows in
    * sequence (the rows may be summed by different threads) */
-  double* rows = (double*)calloc((size_t)p->ny * (F + 1), sizeof(double));
+  real* rows = (real*)calloc((size_t)p->ny * (F + 1), sizeof(real));
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < p->ny; ++j) {
-    double v[ORC_MAXF];
-    double* r = rows + (size_t)j * (F + 1);
+    real v[ORC_MAXF];
+    real* r = rows + (size_t)j * (F + 1);
     for (int i = 0; i < p->nx; ++i)
       for (int qy = 0; qy < nqy; ++qy)
         for (int qx = 0; qx < nq; ++qx) {
@@ -413,8 +435,8 @@ static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* 
           r[F] += W;
         }
   }
-  double vol = 0.0;
-  double tot[ORC_MAXF] = {0};
+  real vol = 0.0;
+  real tot[ORC_MAXF] = {0};
   for (int j = 0; j < p->ny; ++j) {
     for (int f = 0; f < F; ++f) tot[f] += rows[(size_t)j * (F + 1) + f];
     vol += rows[(size_t)j * (F + 1) + F];
@@ -427,8 +449,8 @@ static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* 
   /* the max of |u - avg| over all points (order-independent) */
 #pragma omp parallel
   {
-    double loc[ORC_MAXF] = {0};
-    double v[ORC_MAXF];
+    real loc[ORC_MAXF] = {0};
+    real v[ORC_MAXF];
 #pragma omp for schedule(static)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i)
@@ -436,13 +458,13 @@ static void mesh_sigma(const orc_problem* p, const double* u, int mesh, double* 
           for (int qx = 0; qx < nq; ++qx) {
             cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
             for (int f = 0; f < F; ++f) {
-              double e = fabs(v[f] - avg[f]);
-              if (e > loc[f]) loc[f] = e;
+              real e = R_ABS(v[f] - avg[f]);
+              if (RE(e) > RE(loc[f])) loc[f] = e;
             }
           }
 #pragma omp critical
     for (int f = 0; f < F; ++f)
-      if (loc[f] > sig[f]) sig[f] = loc[f];
+      if (RE(loc[f]) > RE(sig[f])) sig[f] = loc[f];
   }
 }
 
@@ -463,8 +485,8 @@ static double factorial(int m) {
  * face is a point and the integral / |e| is the point value).
  * beta_{e,K} is the normal wave speed at K's cell average.
  * Returns 0, or ORC_ENONPHYSICAL if the cell average is not a physical state. */
-static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, int j, const double* sig,
-                      double* delta /* [k+1] */) {
+static int cell_delta(const orc_problem* p, const real* u, int mesh, int i, int j, const real* sig,
+                      real* delta /* [k+1] */) {
   int F = nfields(p), k = p->k, nq = k + 1, d = p->dim;
   int other = 1 - mesh;
   double gx[ORC_MAXQ], gw[ORC_MAXQ];
@@ -472,9 +494,9 @@ static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, in
   double hx = hx_of(p), hy = hy_of(p);
   double xc, yc;
   cell_centre(p, mesh, i, j, &xc, &yc);
-  double avg[ORC_MAXF];
+  real avg[ORC_MAXF];
   for (int f = 0; f < F; ++f) avg[f] = u[sidx(p, mesh, f, 0, j, i)]; /* mode 0 = cell average */
-  double per_field[ORC_MAXF][ORC_MAXQ];
+  real per_field[ORC_MAXF][ORC_MAXQ];
   memset(per_field, 0, sizeof per_field);
   int status = ORC_OK;
 
@@ -482,12 +504,12 @@ static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, in
     int dir = face / 2;
     double side = (face % 2) ? 1.0 : -1.0;
     double nxv = dir == 0 ? side : 0.0, nyv = dir == 1 ? side : 0.0;
-    double beta = wave_speed(p, avg, nxv, nyv);
-    if (beta < 0.0) { status = ORC_ENONPHYSICAL; beta = 0.0; }
+    real beta = wave_speed(p, avg, nxv, nyv);
+    if (RE(beta) < 0.0) { status = ORC_ENONPHYSICAL; beta = 0.0; }
     double he = dir == 0 ? hx : hy;                  /* h_{e,K}: cell width normal to e */
     double elen = d == 2 ? (dir == 0 ? hy : hx) : 1.0; /* |e| */
     for (int m = 0; m <= k; ++m) {
-      double integ[ORC_MAXF] = {0};
+      real integ[ORC_MAXF] = {0};
       for (int s = 0; s < (d == 2 ? 2 : 1); ++s)
         for (int q = 0; q < (d == 2 ? nq : 1); ++q) {
           double t = d == 2 ? s - 0.5 + 0.5 * gx[q] : 0.0;
@@ -497,29 +519,29 @@ static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, in
           int si, sj;
           double oxi, oeta;
           locate(p, other, x, y, &si, &sj, &oxi, &oeta);
-          double sq[ORC_MAXF] = {0};
+          real sq[ORC_MAXF] = {0};
           for (int ax = 0; ax <= m; ++ax) {
             int ay = m - ax;
             if (d == 1 && ay > 0) continue;
-            double a1[ORC_MAXF], a2[ORC_MAXF];
+            real a1[ORC_MAXF], a2[ORC_MAXF];
             cell_eval(p, u, mesh, i, j, xi, d == 2 ? eta : 0.0, ax, ay, a1);
             cell_eval(p, u, other, si, sj, oxi, oeta, ax, ay, a2);
             for (int f = 0; f < F; ++f) {
-              double df = mesh == 0 ? a1[f] - a2[f] : a2[f] - a1[f]; /* u^C - u^D */
+              real df = mesh == 0 ? a1[f] - a2[f] : a2[f] - a1[f]; /* u^C - u^D */
               sq[f] += df * df;
             }
           }
-          for (int f = 0; f < F; ++f) integ[f] += W * sqrt(sq[f]);
+          for (int f = 0; f < F; ++f) integ[f] += W * R_SQRT(sq[f]);
         }
-      double coef = beta * (2.0 * m + 1.0) * pow(he, m - 1.0) / ((2.0 * k - 1.0) * factorial(m) * elen);
+      real coef = beta * (2.0 * m + 1.0) * pow(he, m - 1.0) / ((2.0 * k - 1.0) * factorial(m) * elen);
       for (int f = 0; f < F; ++f)
-        if (sig[f] != 0.0) per_field[f][m] += coef * integ[f] / sig[f];
+        if (RE(sig[f]) != 0.0) per_field[f][m] += coef * integ[f] / sig[f];
     }
   }
   for (int m = 0; m <= k; ++m) {
-    double mx = 0.0;
+    real mx = 0.0;
     for (int f = 0; f < F; ++f)
-      if (per_field[f][m] > mx) mx = per_field[f][m];
+      if (RE(per_field[f][m]) > RE(mx)) mx = per_field[f][m];
     delta[m] = mx;
   }
   return status;
@@ -528,11 +550,11 @@ static int cell_delta(const orc_problem* p, const double* u, int mesh, int i, in
 /* sigma and avg of both meshes (out arrays [2][F]) and delta of every cell
  * ([2][ny][nx][k+1]).  Returns ORC_ENONPHYSICAL if any cell average is not a
  * physical state. */
-int orc_oe_coefficients(const orc_problem* p, const double* u, double* delta, double* sigma, double* avg) {
+int orc_oe_coefficients(const orc_problem* p, const real* u, real* delta, real* sigma, real* avg) {
   int F = nfields(p), K1 = p->k + 1;
   int status = ORC_OK;
   for (int mesh = 0; mesh < 2; ++mesh) {
-    double a[ORC_MAXF], s[ORC_MAXF];
+    real a[ORC_MAXF], s[ORC_MAXF];
     mesh_sigma(p, u, mesh, a, s);
     for (int f = 0; f < F; ++f) {
       if (sigma) sigma[mesh * F + f] = s[f];
@@ -542,7 +564,7 @@ int orc_oe_coefficients(const orc_problem* p, const double* u, double* delta, do
 #pragma omp parallel for collapse(2) schedule(static) reduction(| : bad)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
-        double dl[ORC_MAXQ];
+        real dl[ORC_MAXQ];
         if (cell_delta(p, u, mesh, i, j, s, dl) != ORC_OK) bad = 1;
         for (int m = 0; m < K1; ++m) delta[(((size_t)mesh * p->ny + j) * p->nx + i) * K1 + m] = dl[m];
       }
@@ -553,10 +575,10 @@ int orc_oe_coefficients(const orc_problem* p, const double* u, double* delta, do
 
 /* Decay factor of a mode of total degree deg >= 1 over the OE step of length
  * tau (Eq. (OEstep2D) solved exactly): exp(-tau sum_{m=0}^{min(deg,k)} delta^m). */
-static double oe_factor(const orc_problem* p, const double* dl, int deg, double tau) {
-  double rate = 0.0;
+static real oe_factor(const orc_problem* p, const real* dl, int deg, real tau) {
+  real rate = 0.0;
   for (int q = 0; q <= p->k && q <= deg; ++q) rate += dl[q];
-  return exp(-tau * rate);
+  return R_EXP(-tau * rate);
 }
 
 /* Sampled evaluation for checks on meshes too large for a whole-mesh oracle
@@ -570,19 +592,19 @@ static double oe_factor(const orc_problem* p, const double* dl, int deg, double 
  *                  NULL, their coefficients after the OE step of length tau
  *                  (out [n][F][M]).  Returns ORC_ENONPHYSICAL if a listed
  *                  cell's average is not a physical state. */
-void orc_rhs_cells(const orc_problem* p, const double* u, double tau_max, int n, const int* cells, double* L) {
+void orc_rhs_cells(const orc_problem* p, const real* u, real tau_max, int n, const int* cells, real* L) {
   int F = nfields(p), M = nmodes(p);
-  double inv = 1.0 / tau_max;
+  real inv = 1.0 / tau_max;
 #pragma omp parallel for schedule(static)
   for (int c = 0; c < n; ++c) cell_rhs(p, u, inv, cells[3 * c], cells[3 * c + 1], cells[3 * c + 2], L + (size_t)c * F * M);
 }
 
-int orc_oe_cells(const orc_problem* p, const double* u, double tau, int n, const int* cells, double* delta,
-                 double* sigma, double* avg, double* usig) {
+int orc_oe_cells(const orc_problem* p, const real* u, real tau, int n, const int* cells, real* delta,
+                 real* sigma, real* avg, real* usig) {
   int F = nfields(p), K1 = p->k + 1;
   int ma[ORC_MAXM], mb[ORC_MAXM];
   int M = modes(p, ma, mb);
-  double s[2][ORC_MAXF], a[2][ORC_MAXF];
+  real s[2][ORC_MAXF], a[2][ORC_MAXF];
   for (int mesh = 0; mesh < 2; ++mesh) {
     mesh_sigma(p, u, mesh, a[mesh], s[mesh]);
     for (int f = 0; f < F; ++f) {
@@ -594,12 +616,12 @@ int orc_oe_cells(const orc_problem* p, const double* u, double tau, int n, const
 #pragma omp parallel for schedule(static) reduction(| : bad)
   for (int c = 0; c < n; ++c) {
     int mesh = cells[3 * c], i = cells[3 * c + 1], j = cells[3 * c + 2];
-    double dl[ORC_MAXQ];
+    real dl[ORC_MAXQ];
     if (cell_delta(p, u, mesh, i, j, s[mesh], dl) != ORC_OK) bad = 1;
     for (int m = 0; m < K1; ++m) delta[(size_t)c * K1 + m] = dl[m];
     if (usig) {
       for (int m = 0; m < M; ++m) {
-        double fac = m > 0 ? oe_factor(p, dl, ma[m] + mb[m], tau) : 1.0;
+        real fac = m > 0 ? oe_factor(p, dl, ma[m] + mb[m], tau) : 1.0;
         for (int f = 0; f < F; ++f) usig[((size_t)c * F + f) * M + m] = u[sidx(p, mesh, f, m, j, i)] * fac;
       }
     }
@@ -612,15 +634,15 @@ int orc_oe_cells(const orc_problem* p, const double* u, double tau, int n, const
  * degree >= max(m, 1) (P^{-1} := P^0), so mode (a, b) obeys
  *   d/dt u_ab = -( sum_{m=0}^{min(a+b, k)} delta^m ) u_ab   for a + b >= 1,
  * and the cell average is untouched. */
-void orc_oe_apply(const orc_problem* p, const double* delta, double tau, double* u) {
+void orc_oe_apply(const orc_problem* p, const real* delta, real tau, real* u) {
   int ma[ORC_MAXM], mb[ORC_MAXM];
   int M = modes(p, ma, mb), F = nfields(p), K1 = p->k + 1;
   for (int mesh = 0; mesh < 2; ++mesh)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
-        const double* dl = delta + (((size_t)mesh * p->ny + j) * p->nx + i) * K1;
+        const real* dl = delta + (((size_t)mesh * p->ny + j) * p->nx + i) * K1;
         for (int m = 1; m < M; ++m) {
-          double fac = oe_factor(p, dl, ma[m] + mb[m], tau);
+          real fac = oe_factor(p, dl, ma[m] + mb[m], tau);
           for (int f = 0; f < F; ++f) u[sidx(p, mesh, f, m, j, i)] *= fac;
         }
       }
@@ -628,10 +650,10 @@ void orc_oe_apply(const orc_problem* p, const double* delta, double tau, double*
 
 /* The OE step F_tau applied in place to both meshes.  k = 0 has no modes to
  * damp and (2k-1) < 0, so the step is the identity there. */
-int orc_oe(const orc_problem* p, double* u, double tau) {
+int orc_oe(const orc_problem* p, real* u, real tau) {
   if (p->k == 0) return ORC_OK;
   size_t nd = (size_t)2 * p->ny * p->nx * (p->k + 1);
-  double* delta = (double*)malloc(nd * sizeof(double));
+  real* delta = (real*)malloc(nd * sizeof(real));
   int st = orc_oe_coefficients(p, u, delta, NULL, NULL);
   orc_oe_apply(p, delta, tau, u);
   free(delta);
@@ -644,42 +666,42 @@ int orc_oe(const orc_problem* p, double* u, double tau) {
  * Section 4): 1D  C_CFL h / beta;  2D  C_CFL / (beta_x/h_x + beta_y/h_y), with
  * beta the maximum wave speed over the cell averages of both meshes.
  * Returns ORC_ENONPHYSICAL on a non-physical cell average. */
-int orc_tau_max(const orc_problem* p, const double* u, double* tau_max) {
+int orc_tau_max(const orc_problem* p, const real* u, real* tau_max) {
   int F = nfields(p);
-  double bxm = 0.0, bym = 0.0;
+  real bxm = 0.0, bym = 0.0;
   int st = ORC_OK;
   for (int mesh = 0; mesh < 2; ++mesh)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
-        double w[ORC_MAXF];
+        real w[ORC_MAXF];
         for (int f = 0; f < F; ++f) w[f] = u[sidx(p, mesh, f, 0, j, i)];
-        double sx = wave_speed(p, w, 1.0, 0.0);
-        double sy = p->dim == 2 ? wave_speed(p, w, 0.0, 1.0) : 0.0;
-        if (sx < 0.0 || sy < 0.0) { st = ORC_ENONPHYSICAL; continue; }
-        if (sx > bxm) bxm = sx;
-        if (sy > bym) bym = sy;
+        real sx = wave_speed(p, w, 1.0, 0.0);
+        real sy = p->dim == 2 ? wave_speed(p, w, 0.0, 1.0) : 0.0;
+        if (RE(sx) < 0.0 || RE(sy) < 0.0) { st = ORC_ENONPHYSICAL; continue; }
+        if (RE(sx) > RE(bxm)) bxm = sx;
+        if (RE(sy) > RE(bym)) bym = sy;
       }
   double hx = hx_of(p), hy = hy_of(p);
-  double rate = bxm / hx + (p->dim == 2 ? bym / hy : 0.0);
-  *tau_max = rate > 0.0 ? p->cfl / rate : 0.0;
+  real rate = bxm / hx + (p->dim == 2 ? bym / hy : 0.0);
+  *tau_max = RE(rate) > 0.0 ? p->cfl / rate : 0.0;
   return st;
 }
 
 /* One stage combination of the Shu-Osher form: out = sum_m c_m U_m + tau d L(U_last). */
-static void axpy_stage(size_t n, double* out, const double* a, double ca, const double* b, double cb,
-                       const double* L, double cl) {
+static void axpy_stage(size_t n, real* out, const real* a, double ca, const real* b, double cb,
+                       const real* L, real cl) {
   for (size_t q = 0; q < n; ++q) out[q] = ca * a[q] + cb * b[q] + cl * L[q];
 }
 
 /* One full time step of Eq. (eq:RKCDG) in place: the stages of the chosen RK
  * method, each followed by the OE step F_tau (if enabled). */
-int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
+int orc_step_tau(const orc_problem* p, real* u, real tau, real tau_max) {
   int F = nfields(p), M = nmodes(p);
   size_t n = (size_t)2 * F * M * p->ny * p->nx;
-  double* L = (double*)malloc(n * sizeof(double));
-  double* u1 = (double*)malloc(n * sizeof(double));
-  double* u2 = (double*)malloc(n * sizeof(double));
-  double* u3 = (double*)malloc(n * sizeof(double));
+  real* L = (real*)malloc(n * sizeof(real));
+  real* u1 = (real*)malloc(n * sizeof(real));
+  real* u2 = (real*)malloc(n * sizeof(real));
+  real* u3 = (real*)malloc(n * sizeof(real));
   int st = ORC_OK, s;
 #define OE(x)                          \
   do {                                 \
@@ -692,7 +714,7 @@ int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
     orc_rhs(p, u, tau_max, L);
     axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
     OE(u1);
-    memcpy(u, u1, n * sizeof(double));
+    memcpy(u, u1, n * sizeof(real));
   } else if (p->rk == 2) {
     orc_rhs(p, u, tau_max, L);
     axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
@@ -700,7 +722,7 @@ int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
     orc_rhs(p, u1, tau_max, L);
     axpy_stage(n, u2, u, 0.5, u1, 0.5, L, 0.5 * tau);
     OE(u2);
-    memcpy(u, u2, n * sizeof(double));
+    memcpy(u, u2, n * sizeof(real));
   } else if (p->rk == 3) {
     orc_rhs(p, u, tau_max, L);
     axpy_stage(n, u1, u, 1.0, u, 0.0, L, tau);
@@ -711,10 +733,10 @@ int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
     orc_rhs(p, u2, tau_max, L);
     axpy_stage(n, u3, u, 1.0 / 3.0, u2, 2.0 / 3.0, L, 2.0 / 3.0 * tau);
     OE(u3);
-    memcpy(u, u3, n * sizeof(double));
+    memcpy(u, u3, n * sizeof(real));
   } else {
     /* classical RK4 in Shu-Osher form */
-    double* u4 = (double*)malloc(n * sizeof(double));
+    real* u4 = (real*)malloc(n * sizeof(real));
     orc_rhs(p, u, tau_max, L);
     axpy_stage(n, u1, u, 1.0, u, 0.0, L, 0.5 * tau);
     OE(u1);
@@ -728,7 +750,7 @@ int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
     for (size_t q = 0; q < n; ++q)
       u4[q] = -u[q] / 3.0 + u1[q] / 3.0 + 2.0 * u2[q] / 3.0 + u3[q] / 3.0 + tau / 6.0 * L[q];
     OE(u4);
-    memcpy(u, u4, n * sizeof(double));
+    memcpy(u, u4, n * sizeof(real));
     free(u4);
   }
 #undef OE
@@ -744,25 +766,26 @@ int orc_step_tau(const orc_problem* p, double* u, double tau, double tau_max) {
  * except that the step that reaches T_end is clipped to T_end - t (and a step
  * that would leave a sliver shorter than 1e-12 T_end is stretched to T_end).
  * Returns the status; *t is advanced and *steps_done counts the steps taken. */
-int orc_advance(const orc_problem* p, double* u, double* t, double T_end, int nsteps, int* steps_done) {
+int orc_advance(const orc_problem* p, real* u, double* t, double T_end, int nsteps, int* steps_done) {
   int st = ORC_OK;
   int done = 0;
   for (int s = 0; s < nsteps; ++s) {
     if (T_end > 0.0 && *t >= T_end) break;
-    double tm;
+    real tm;
     int q = orc_tau_max(p, u, &tm);
     if (q != ORC_OK) { st = q; break; }
-    double tau = tm;
-    if (T_end > 0.0 && (T_end - (*t + tm) < 1e-12 * T_end)) tau = T_end - *t;
+    real tau = tm;
+    if (T_end > 0.0 && (T_end - (*t + RE(tm)) < 1e-12 * T_end)) tau = T_end - *t;
     q = orc_step_tau(p, u, tau, tm);
     if (q != ORC_OK) st = q;
-    *t = (T_end > 0.0 && tau == T_end - *t) ? T_end : *t + tau;
+    *t = (T_end > 0.0 && RE(tau) == T_end - *t) ? T_end : *t + RE(tau);
     ++done;
   }
   if (steps_done) *steps_done = done;
   return st;
 }
 
+#ifndef ORC_COMPLEX_STEP
 /* ------------------------------------------------- initial projection --- */
 
 /* Composite Gauss points for sampling the initial data: on every stored cell
@@ -854,6 +877,8 @@ void orc_eval_points(const orc_problem* p, const double* u, int mesh, size_t n, 
   int F = nfields(p), d = p->dim;
   for (size_t q = 0; q < n; ++q) point_eval(p, u, mesh, xy[q * d], d == 2 ? xy[q * d + 1] : 0.0, out + q * F);
 }
+
+#endif /* ORC_COMPLEX_STEP */
 
 int orc_num_threads(void) {
 #ifdef _OPENMP

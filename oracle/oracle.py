@@ -20,6 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oecdg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboecdg_oracle.so")
+_SRC_CS = os.path.join(_HERE, "oecdg_oracle_cs.c")
+_LIB_CS = os.path.join(_BUILD, "liboecdg_oracle_cs.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
@@ -38,15 +40,21 @@ class _Problem(ctypes.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle library (idempotent).  Returns its path."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+def _compile(src: str, out: str, deps, force: bool) -> None:
+    if force or not os.path.exists(out) or any(os.path.getmtime(out) < os.path.getmtime(d) for d in deps):
+        tmp = out + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
-               "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm"]
+               "-D_GNU_SOURCE", "-o", tmp, src, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
+        os.replace(tmp, out)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library and its complex-step build (idempotent).
+    Returns the path of the former."""
+    os.makedirs(_BUILD, exist_ok=True)
+    _compile(_SRC, _LIB, [_SRC], force)
+    _compile(_SRC_CS, _LIB_CS, [_SRC, _SRC_CS], force)
     return _LIB
 
 
@@ -320,3 +328,55 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     lib().orc_set_num_threads(n)
+
+
+# ------------------------------------------------------------- complex step --
+
+_lib_cs_handle = None
+
+
+def lib_cs():
+    """The complex-step build of the oracle (oracle/oecdg_oracle_cs.c)."""
+    global _lib_cs_handle
+    if _lib_cs_handle is None:
+        build()
+        L = ctypes.CDLL(_LIB_CS)
+        P = ctypes.POINTER(_Problem)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_advance.restype = ctypes.c_int
+        L.orc_advance.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.orc_step_jacobian.restype = ctypes.c_int
+        L.orc_step_jacobian.argtypes = [P, dp, ctypes.c_int, ctypes.c_double, dp]
+        _lib_cs_handle = L
+    return _lib_cs_handle
+
+
+def step_jvp(p: Problem, u: np.ndarray, v: np.ndarray, nsteps: int = 1, h: float = 1e-30):
+    """(step(u), J v) for nsteps steps (tau from the state, no end time) by the
+    complex step: the oracle run on u + i h v.  Returns (real part, Im / h,
+    status)."""
+    z = np.ascontiguousarray(np.asarray(u, dtype=np.float64) + 1j * h * np.asarray(v, dtype=np.float64))
+    t = ctypes.c_double(0.0)
+    done = ctypes.c_int(0)
+    pc = p.c()
+    st = lib_cs().orc_advance(ctypes.byref(pc), z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(t),
+                              0.0, nsteps, ctypes.byref(done))
+    return z.real.copy(), z.imag / h, st
+
+
+def step_jacobian(p: Problem, u: np.ndarray, nsteps: int = 1, h: float = 1e-30):
+    """The oracle's Jacobian of nsteps steps at u, one complex-step run per
+    column: J [n, n] with J[r, q] = d step_r / d u_q (flattened state order).
+    Returns (J, status)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.size
+    J = np.zeros((n, n))
+    pc = p.c()
+    st = lib_cs().orc_step_jacobian(ctypes.byref(pc), _dp(u), nsteps, h, _dp(J))
+    return J, st
+
+
+def step_adjoint(p: Problem, u: np.ndarray, lam: np.ndarray, nsteps: int = 1):
+    """The oracle's adjoint of nsteps steps at u: J^T lam, shaped like u."""
+    J, st = step_jacobian(p, u, nsteps)
+    return (J.T @ np.asarray(lam, dtype=np.float64).ravel()).reshape(np.shape(u)), st

@@ -564,3 +564,59 @@ def test_sampled_cells_match_whole_mesh(dim, k, basis, system, bc):
         np.testing.assert_array_equal(Ls[q], L[m, :, :, j, i])
         np.testing.assert_array_equal(ds[q], d[m, j, i])
         np.testing.assert_array_equal(us[q], uo[m, :, :, j, i])
+
+
+# ------------------------------------------- complex-step build of the oracle
+
+def _cs_problem(system, oe=1):
+    p = O.Problem(dim=2, nx=6, ny=5, k=2, system=system, bc=O.PERIODIC, rk=3, cfl=0.2, bx=2.0, by=2.0,
+                  adv_x=1.0, adv_y=0.6, oe=oe)
+    u = W.random_modal(p.shape, 4, 0.05)
+    if system == O.EULER:
+        u[:, 0, 0] += 1.0
+        u[:, 3, 0] += 2.5
+    return p, u
+
+
+@pytest.mark.parametrize("system", [O.ADVECTION, O.EULER])
+def test_complex_step_real_part_is_the_oracle_step(system):
+    p, u = _cs_problem(system)
+    f, jv, st = O.step_jvp(p, u, W.random_modal(p.shape, 5, 1.0))
+    ref, _, _, st2 = O.advance(p, u, 0.0, 0.0, 1)
+    assert st == st2 == O.OK
+    assert np.abs(f - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("system", [O.ADVECTION, O.EULER])
+def test_complex_step_jvp_matches_central_differences(system):
+    """The complex-step derivative of one step (OE on, tau from the state)
+    against central differences of the plain oracle: the differences carry an
+    O(eps^2) truncation and O(1e-16 / eps) rounding error, ~1e-9 at eps = 1e-6."""
+    p, u = _cs_problem(system)
+    v = W.random_modal(p.shape, 5, 1.0)
+    _, jv, _ = O.step_jvp(p, u, v)
+    eps = 1e-6
+    fd = (O.advance(p, u + eps * v, 0.0, 0.0, 1)[0] - O.advance(p, u - eps * v, 0.0, 0.0, 1)[0]) / (2 * eps)
+    assert np.abs(jv - fd).max() <= 1e-8 * np.abs(jv).max()
+
+
+def test_complex_step_is_exact_on_a_linear_step():
+    """Advection without the OE step: tau does not depend on the state and the
+    step is linear, so J v is the plain oracle's step applied to v itself (no
+    difference quotient involved)."""
+    p, u = _cs_problem(O.ADVECTION, oe=0)
+    v = W.random_modal(p.shape, 6, 1.0)
+    _, jv, _ = O.step_jvp(p, u, v)
+    ref = O.advance(p, v, 0.0, 0.0, 1)[0]
+    assert np.abs(jv - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_complex_step_jacobian_columns():
+    p = O.Problem(dim=2, nx=3, ny=3, k=2, system=O.ADVECTION, bc=O.PERIODIC, rk=3, cfl=0.2, adv_x=1.0, adv_y=0.6)
+    u = W.random_modal(p.shape, 7, 0.1)
+    J, st = O.step_jacobian(p, u)
+    assert st == O.OK and J.shape == (u.size, u.size)
+    for seed in (1, 2):
+        v = W.random_modal(p.shape, seed, 1.0)
+        _, jv, _ = O.step_jvp(p, u, v)
+        assert np.abs(J @ v.ravel() - jv.ravel()).max() <= 1e-13 * np.abs(jv).max()
