@@ -399,6 +399,61 @@ def run_generic(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_time_to_solution(args, ws, rank, local):
+    """The two 1D workloads run to their end time (1D advection, 128 cells,
+    T = 2 pi; 1D Euler Shu-Osher, 4000 cells, T = 1.8): launch-bound, so the
+    figure is the time to solution, with one launch per kernel
+    (cdg_step_async) and with the step replayed as a CUDA graph
+    (cdg_step_graph); the two results must be identical."""
+    import torch
+    from paper_2503_12473_gb300 import oecdg as G
+    from paper_2503_12473_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    G.load()
+    w = W.advection_1d(128) if args.workload == "advection-1d" else W.shu_osher_1d(4000)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w), stream=stream)
+    with torch.cuda.stream(stream):
+        u0 = ctx.project(w.u0)
+        # steps to T: one untimed pass, one step at a time
+        uw = u0.clone()
+        t, nsteps = 0.0, 0
+        while t < w.T:
+            ctx.cdg_step_async(uw, t, w.T, 1)
+            t = ctx.cdg_get_time()
+            nsteps += 1
+        res = {}
+        for mode in ("kernels", "graph"):
+            u = u0.clone()
+            step = ctx.cdg_step_async if mode == "kernels" else ctx.cdg_step_graph
+            step(u, 0.0, w.T, 3)  # warm-up (and, for the graph, its capture for this u)
+            u.copy_(u0)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            l0 = ctx.cdg_launch_count()
+            ev0.record(stream)
+            step(u, 0.0, w.T, nsteps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if ctx.cdg_check_status() != G.CDG_OK:
+                raise RuntimeError("non-physical state")
+            res[mode] = (ev0.elapsed_time(ev1), ctx.cdg_launch_count() - l0, u, ctx.cdg_get_time())
+    same = bool(torch.equal(res["kernels"][2], res["graph"][2]))
+    dof = ctx.cdg_state_numel()
+    line = {"metric": f"time to solution, {w.name} to T = {w.T:.6g}", "workload": w.name, "steps": nsteps,
+            "dof": dof, "t_final": res["graph"][3],
+            "kernels": {"ms": res["kernels"][0], "us_per_step": 1e3 * res["kernels"][0] / nsteps,
+                        "gpu_launches": res["kernels"][1]},
+            "graph": {"ms": res["graph"][0], "us_per_step": 1e3 * res["graph"][0] / nsteps,
+                      "gpu_launches": res["graph"][1]},
+            "speedup_graph": res["kernels"][0] / res["graph"][0], "identical": same,
+            "dof_updates_per_s_graph": 3.0 * dof * nsteps / (res["graph"][0] * 1e-3),
+            "unit_time": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args, ws, rank, local):
     """256 independent periodic 2D Euler Q^2 problems (seeded sizes in
     {64,...,512}^2 and data): one graph-captured batched launch per phase
@@ -546,10 +601,12 @@ def main():
     ap.add_argument("--n", type=int, default=1024, help="cells per direction (the workload is 1024)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched", "adjoint", "steady-wave"],
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "batched", "adjoint", "steady-wave", "advection-1d",
+                                                       "shu-osher"],
                     help="riemann: the metric's workload (default); batched: 256 uneven meshes; "
                          "adjoint: gradient of the vortex loss (cost and finite-difference check); "
-                         "steady-wave: the degree-generic 2D kernels on the smooth Euler test of Table 4")
+                         "steady-wave: the degree-generic 2D kernels on the smooth Euler test of Table 4; "
+                         "advection-1d, shu-osher: time to solution of the 1D workloads")
     ap.add_argument("--k", type=int, default=3, help="steady-wave: degree 1..3")
     ap.add_argument("--basis", default="P", choices=["P", "Q"], help="steady-wave: P^k or Q^k")
     ap.add_argument("--fd-dirs", type=int, default=4)
@@ -567,6 +624,8 @@ def main():
         run_adjoint(args, ws, rank, local)
     elif args.workload == "steady-wave":
         run_generic(args, ws, rank, local)
+    elif args.workload in ("advection-1d", "shu-osher"):
+        run_time_to_solution(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -168,6 +168,19 @@ cdg_status cdg_step(cdg_ctx* ctx, double* d_u, double t, double T_end, int nstep
  * the device (cdg_get_time). */
 cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
 
+/* As cdg_step_async, for many small steps: the kernels of one step (Eq.
+ * (eq:RKCDG), the same launches as cdg_step_async) are captured once into a
+ * CUDA graph on the context's stream, and the graph is replayed nsteps times,
+ * one graph launch per step instead of one launch per kernel.  tau, tau_max
+ * and t stay on the device, so replays need no host work; steps after T_end
+ * is reached are skipped on the device as in cdg_step.  The graph is bound to
+ * d_u and T_end: a call with another d_u or T_end captures a new one (after a
+ * stream synchronisation).  Needs a context created with its own stream
+ * (CDG_EINVAL with the legacy default stream).  Kernel timing
+ * (cdg_profile_begin) does not see replayed steps.  Asynchronous; check the
+ * status with cdg_check_status. */
+cdg_status cdg_step_graph(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
+
 /* Device time after the last cdg_step / cdg_step_async; synchronises. */
 cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
 

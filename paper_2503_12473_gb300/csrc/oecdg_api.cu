@@ -18,7 +18,7 @@ using namespace oecdg;
 enum { PROF_STAGE = 0, PROF_OE = 1 };
 
 static void prof_mark(cdg_ctx* c, int cls, int stop) {
-  if (!c->prof_on) return;
+  if (!c->prof_on || c->capturing) return;
   const int n = c->prof_n[cls];
   if (n >= c->prof_cap) return;
   cudaEventRecord(c->prof_ev[cls][2 * n + stop], c->stream);
@@ -142,6 +142,7 @@ cdg_status cdg_free(cdg_ctx* c) {
   cudaFree(c->buf_b);
   cudaFree(c->buf_c);
   cudaFree(c->buf_d);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   cudaFree(c->partials);
   cudaFree(c->wave_partial);
   cudaFree(c->dt);
@@ -409,6 +410,26 @@ cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta
   return CDG_OK;
 }
 
+// The kernels of one time step on d_u (no host synchronisation): wave speed
+// and tau, then every stage of the context's RK method with the OE step.
+static cudaError_t enqueue_step(cdg_ctx* ctx, double* d_u, double T_end) {
+  const int rk = ctx->d.rk, nst = n_stages(rk);
+  // U[l]: the damped stage values.  u_h of every stage -> buf_a; u_sigma ->
+  // buf_b (RK4: stages 1..3 -> buf_b, buf_c, buf_d), the last one back into d_u.
+  const double* U[4] = {d_u, ctx->buf_b, rk == CDG_RK_RK4 ? ctx->buf_c : ctx->buf_b,
+                        rk == CDG_RK_RK4 ? ctx->buf_d : ctx->buf_b};
+  cudaError_t e = launch_dt(ctx, d_u, T_end);
+  if (e != cudaSuccess) return e;
+  for (int l = 0; l < nst; ++l) {
+    if ((e = run_stage(ctx, 0, U[l], rk_comb(rk, l, U), ctx->buf_a, ctx->dt)) != cudaSuccess) return e;
+    double* dst = (l == nst - 1) ? d_u : (double*)U[l + 1];
+    if (ctx->d.oe) e = run_oe(ctx, ctx->buf_a, dst, nullptr);
+    else e = cudaMemcpyAsync(dst, ctx->buf_a, ctx->numel * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
   if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "step: null pointer");
   if (nsteps < 0) return fail(ctx, CDG_EINVAL, "step: nsteps < 0");
@@ -416,24 +437,50 @@ cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int
     return fail(ctx, CDG_EINVAL, "step: d_u is a context buffer");
   CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step");
   ctx->launches += 1;
-  const int rk = ctx->d.rk, nst = n_stages(rk);
-  // U[l]: the damped stage values.  u_h of every stage -> buf_a; u_sigma ->
-  // buf_b (RK4: stages 1..3 -> buf_b, buf_c, buf_d), the last one back into d_u.
-  const double* U[4] = {d_u, ctx->buf_b, rk == CDG_RK_RK4 ? ctx->buf_c : ctx->buf_b,
-                        rk == CDG_RK_RK4 ? ctx->buf_d : ctx->buf_b};
-  for (int s = 0; s < nsteps; ++s) {
-    CK(launch_dt(ctx, d_u, T_end), "step: dt");
-    for (int l = 0; l < nst; ++l) {
-      CK(run_stage(ctx, 0, U[l], rk_comb(rk, l, U), ctx->buf_a, ctx->dt), "step: stage");
-      double* dst = (l == nst - 1) ? d_u : (double*)U[l + 1];
-      if (ctx->d.oe) {
-        CK(run_oe(ctx, ctx->buf_a, dst, nullptr), "step: oe");
-      } else {
-        CK(cudaMemcpyAsync(dst, ctx->buf_a, ctx->numel * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
-           "step: copy");
-      }
+  for (int s = 0; s < nsteps; ++s) CK(enqueue_step(ctx, d_u, T_end), "step");
+  return CDG_OK;
+}
+
+cdg_status cdg_step_graph(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
+  if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "step_graph: null pointer");
+  if (nsteps < 0) return fail(ctx, CDG_EINVAL, "step_graph: nsteps < 0");
+  if (!ctx->stream) return fail(ctx, CDG_EINVAL, "step_graph: the context needs its own stream");
+  if (d_u == ctx->buf_a || d_u == ctx->buf_b || d_u == ctx->buf_c || d_u == ctx->buf_d)
+    return fail(ctx, CDG_EINVAL, "step_graph: d_u is a context buffer");
+  if (!ctx->graph_exec || ctx->graph_u != d_u || ctx->graph_tend != T_end) {
+    if (ctx->graph_exec) {
+      CK(cudaStreamSynchronize(ctx->stream), "step_graph");
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const long long l0 = ctx->launches;
+    ctx->capturing = 1;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e2 = e == cudaSuccess ? enqueue_step(ctx, d_u, T_end) : e;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->capturing = 0;
+    ctx->launches = l0;
+    if (e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      return cuda_fail(ctx, e, "step_graph: capture");
+    }
+    ctx->graph_u = d_u;
+    ctx->graph_tend = T_end;
+    ctx->graph_launches = 0;
+    {
+      // count the kernels of one step (the same launches as enqueue_step)
+      const int nst = n_stages(ctx->d.rk);
+      ctx->graph_launches = 2 + (long long)nst * (1 + (ctx->d.oe ? 2 : 0));
     }
   }
+  CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step_graph");
+  ctx->launches += 1;
+  for (int s = 0; s < nsteps; ++s) CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "step_graph: launch");
+  ctx->launches += ctx->graph_launches * nsteps;
   return CDG_OK;
 }
 

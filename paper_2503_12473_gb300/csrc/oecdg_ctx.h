@@ -33,6 +33,12 @@ struct cdg_ctx {
   double* avg;           // [2][F]
   int* status;           // status bits
   long long launches;
+  // cdg_step_graph: one captured step, valid for (graph_u, graph_tend)
+  cudaGraphExec_t graph_exec;
+  double* graph_u;
+  double graph_tend;
+  long long graph_launches;  // kernels in one captured step
+  int capturing;             // no profiling events while capturing
   // optional per-kernel timing (cdg_profile_begin / cdg_profile_end)
   int prof_on;
   int prof_cap;

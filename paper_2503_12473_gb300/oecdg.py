@@ -32,7 +32,7 @@ EXPORTED = [
     "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
     "cdg_step_adjoint", "cdg_batch_set_rows", "cdg_record_numel", "cdg_step_record", "cdg_step_adjoint_recorded",
-    "cdg_rk_combine",
+    "cdg_rk_combine", "cdg_step_graph",
 ]
 
 
@@ -106,6 +106,8 @@ def load(build_if_missing: bool = True):
     L.cdg_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.cdg_step_async.restype = st
     L.cdg_step_async.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.cdg_step_graph.restype = st
+    L.cdg_step_graph.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.cdg_get_time.restype = st
     L.cdg_get_time.argtypes = [vp, dp]
     L.cdg_check_status.restype = st
@@ -307,6 +309,9 @@ class Context:
 
     def cdg_step_async(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
         self._ck(self._L.cdg_step_async(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_async")
+
+    def cdg_step_graph(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
+        self._ck(self._L.cdg_step_graph(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_graph")
 
     def cdg_step_adjoint(self, d_un, d_lam_next, d_lam, d_gtau=None):
         self._ck(self._L.cdg_step_adjoint(self.h, _ptr(d_un), _ptr(d_lam_next), _ptr(d_lam), _ptr(d_gtau)),

@@ -236,3 +236,42 @@ def test_scope_checks():
     with pytest.raises(G.CdgError) as e:
         ctx.cdg_rk_stage(3, u, u.clone(), torch.empty_like(u))
     assert e.value.status == G.CDG_EINVAL
+
+
+@pytest.mark.parametrize("name", ["advection", "shu_osher"])
+def test_step_graph_equals_step(name):
+    """cdg_step_graph (one captured step replayed) gives cdg_step_async's
+    result bit for bit, including the clipped last step at T_end and the
+    skipped steps after it; a second call with another state re-captures."""
+    from paper_2503_12473_gb300 import oecdg as G
+    w = W.advection_1d(128) if name == "advection" else W.shu_osher_1d(400)
+    T = w.T if name == "advection" else 0.01
+    st = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w), stream=st)
+    with torch.cuda.stream(st):
+        u0 = ctx.project(w.u0)
+        a = u0.clone()
+        b = u0.clone()
+        c = u0.clone()
+    n = 1400 if name == "advection" else 300
+    ctx.cdg_step_async(a, 0.0, T, n)
+    ta = ctx.cdg_get_time()
+    ctx.cdg_step_graph(b, 0.0, T, n // 2)
+    tb = ctx.cdg_get_time()
+    ctx.cdg_step_graph(b, tb, T, n - n // 2)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert ctx.cdg_get_time() == ta
+    assert torch.equal(a, b)
+    ctx.cdg_step_graph(c, 0.0, T, n)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert torch.equal(a, c)
+
+
+def test_step_graph_needs_own_stream():
+    from paper_2503_12473_gb300 import oecdg as G
+    w = W.advection_1d(64)
+    ctx = G.Context(G.desc_from_workload(w))
+    u = ctx.project(w.u0)
+    with pytest.raises(G.CdgError) as e:
+        ctx.cdg_step_graph(u, 0.0, 0.0, 2)
+    assert e.value.status == G.CDG_EINVAL
