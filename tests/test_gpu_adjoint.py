@@ -113,7 +113,8 @@ def test_step_adjoint_equals_oracle_adjoint(system, nx, ny):
 
 def test_step_adjoint_dot_products_vs_oracle_jvp():
     """On a 20 x 20 vortex state: <lam, J v> with J v from the complex-step
-    oracle against <J^T lam, v> from the CUDA adjoint, four seeded directions.
+    oracle against <J^T lam, v> from the CUDA adjoint, 64 seeded directions, to
+    1e-11 (measured: max 1.6e-12, median 7e-15).
     Both sides get the same host-built state (oracle projection + seeded
     perturbation, 5% offset between the meshes)."""
     from paper_2503_12473_gb300 import oecdg as G
@@ -131,13 +132,13 @@ def test_step_adjoint_dot_products_vs_oracle_jvp():
     ctx.cdg_step_adjoint(torch.from_numpy(u).cuda(), torch.from_numpy(lam).cuda(), adj)
     torch.cuda.synchronize()
     a = adj.cpu().numpy()
-    for _ in range(4):
+    for _ in range(64):
         v = rng.standard_normal(u.shape)
         _, jv, st = O.step_jvp(p, u, v)
         assert st == O.OK
         lhs = float((a * v).sum())
         rhs = float((lam * jv).sum())
-        assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+        assert abs(lhs - rhs) <= 1e-11 * abs(rhs), (lhs, rhs)
 
 
 def test_adjoint_gtau_matches_fd_of_fixed_tau_step():
