@@ -440,7 +440,7 @@ def test_table1_advection_accuracy(k, rk, cfl):
     assert abs(mine - paper) < 0.35, (mine, paper)
 
 
-def test_config1_order_one_period():
+def test_advection_p2_order_over_one_period():
     """1D advection of sin x on [0, 2 pi] over one period with P^2, SSP-RK3,
     CFL 0.1: the error decreases at least at order k + 1 = 3 (error theorem,
     Section 3.3, an upper bound)."""
