@@ -68,11 +68,11 @@ __global__ void k_sigma(const double* __restrict__ partials, long long nblk, int
 // over fields (Remark on systems); delta = 0 where sigma = 0.  Mode (a,b) then
 // decays by exp(-tau sum_{m <= min(a+b, 2)} delta^m), the average is kept.
 // Damping coefficients and the exact OE step of every cell (oe_cell2d).
-template <int SYS, int BC, bool WRITE_DELTA>
+template <int SYS, int BC, bool WRITE_DELTA, bool ISO>
 __global__ void __launch_bounds__(NT, OECDG_OE_MINB) k_oe2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                              const double* __restrict__ dt, const double* __restrict__ sigma,
                                              double* __restrict__ delta_out, int* __restrict__ status) {
-  oe_cell2d<SYS, BC, WRITE_DELTA>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.z,
+  oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.z,
                                   blockIdx.x * TX + (threadIdx.x % TX), blockIdx.y * TY + (threadIdx.x / TX));
 }
 
@@ -236,10 +236,16 @@ cudaError_t launch_sigma(const double* partials, long long nblk, int F, long lon
 template <int SYS, int BC>
 static cudaError_t oe2d_t(const Geo& g, const double* uh, double* usig, const double* dt, const double* sigma,
                           double* delta, int* status, cudaStream_t st) {
-  if (delta)
-    k_oe2d<SYS, BC, true><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+  // square cells: the isotropic variant of the OE body (same result up to rounding)
+  const bool iso = g.hx == g.hy;
+  if (delta && iso)
+    k_oe2d<SYS, BC, true, true><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+  else if (delta)
+    k_oe2d<SYS, BC, true, false><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+  else if (iso)
+    k_oe2d<SYS, BC, false, true><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
   else
-    k_oe2d<SYS, BC, false><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+    k_oe2d<SYS, BC, false, false><<<tile_grid(g), NT, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
   return cudaGetLastError();
 }
 

@@ -285,7 +285,10 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 
 // REC = 1 also records, per cell and order m, (delta^m, the field that gives
 // the max, that field's x- and y-face sums) for the adjoint: rec[cell][3][4].
-template <int SYS, int BC, bool WRITE_DELTA, int REC = 0>
+// ISO = true requires hx == hy: every m-th derivative then carries the same
+// factor (2/h)^m, so the traces stay in reference units and the factor is
+// applied once, in the constants of delta^m (the recorded sums are physical).
+template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false>
 __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
@@ -320,9 +323,12 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     by = fabs(g.adv_y);
   }
   // (2m+1) h^{m-1} / ((2k-1) m!) / 4  (1/4: the half-face rule over |e|)
-  const double cx0 = 1.0 / (12.0 * g.hx), cx1 = 0.25, cx2 = 5.0 * g.hx / 24.0;
-  const double cy0 = 1.0 / (12.0 * g.hy), cy1 = 0.25, cy2 = 5.0 * g.hy / 24.0;
   const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;  // reference -> physical derivative
+  // ISO: the face sums of orders 1 and 2 are in reference units; their
+  // physical factors dx1 and dx1^2 join the constants
+  const double iso1 = ISO ? dx1 : 1.0, iso2 = ISO ? dx1 * dx1 : 1.0;
+  const double cx0 = 1.0 / (12.0 * g.hx), cx1 = 0.25 * iso1, cx2 = 5.0 * g.hx / 24.0 * iso2;
+  const double cy0 = 1.0 / (12.0 * g.hy), cy1 = 0.25 * iso1, cy2 = 5.0 * g.hy / 24.0 * iso2;
 
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;  // max over fields
   int rf[3] = {-1, -1, -1};             // REC: field of the max, and its face sums
@@ -391,11 +397,20 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           // physical scalings: normal derivative series (order 1, 2), tangential
           // derivative of the value and of the normal derivative, second
           // tangential derivative (a constant on the half-face)
-          const double a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
-          const double b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
-          const double t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
-          const double m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
-          const double tt = 3.0 * dt2 * e0[2];
+          double a0, a1, a2, b0, b1, b2, t0, t1, m0, m1, tt;
+          if constexpr (ISO) {
+            a0 = e1[0], a1 = e1[1], a2 = e1[2];
+            b0 = e2[0], b1 = e2[1], b2 = e2[2];
+            t0 = e0[1], t1 = 3.0 * e0[2];
+            m0 = a1, m1 = 3.0 * a2;
+            tt = t1;
+          } else {
+            a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
+            b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
+            t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
+            m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
+            tt = 3.0 * dt2 * e0[2];
+          }
           const double tt2 = tt * tt;
           double S0 = 0.0, S1 = 0.0, S2 = 0.0;
 #pragma unroll
@@ -447,8 +462,9 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     for (int m = 0; m < 3; ++m) {
       r[4 * m] = dd[m];
       r[4 * m + 1] = (double)rf[m];
-      r[4 * m + 2] = rs[m][0];
-      r[4 * m + 3] = rs[m][1];
+      const double sc = m == 0 ? 1.0 : (m == 1 ? iso1 : iso2);  // physical sums
+      r[4 * m + 2] = ISO ? rs[m][0] * sc : rs[m][0];
+      r[4 * m + 3] = ISO ? rs[m][1] * sc : rs[m][1];
     }
   }
   if (WRITE_DELTA) {

@@ -502,11 +502,11 @@ __device__ __forceinline__ void beta_and_grad(const Geo& g, const double* w, dou
 
 // Forward OE step that also records (delta^m, field of the max, its face
 // sums) per cell for the adjoint.
-template <int SYS>
+template <int SYS, bool ISO>
 __global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                                  const double* __restrict__ dt, const double* __restrict__ sigma,
                                                  int* __restrict__ status, double* __restrict__ rec) {
-  oe_cell2d<SYS, BC_PERIODIC, false, 1>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
+  oe_cell2d<SYS, BC_PERIODIC, false, 1, ISO>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
                                          blockIdx.x * 32 + (threadIdx.x & 31),
                                          blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec);
 }
@@ -1086,7 +1086,10 @@ static cudaError_t adj_forward(cdg_ctx* c, const double* un, double* const* H, d
     if (oe) {
       if ((e = launch_sigma(c->partials, c->nblk, F, g.plane, c->sigma, c->avg, st)) != cudaSuccess) return e;
       const dim3 grid((g.nx + 31) / 32, (g.ny + AT / 32 - 1) / (AT / 32), 2);
-      k_oe_rec2d<SYS><<<grid, AT, 0, st>>>(g, H[l], dst, dt, c->sigma, c->status, R[l]);
+      // the variant the forward step uses (square cells: isotropic), so the
+      // recorded states equal cdg_step's
+      if (g.hx == g.hy) k_oe_rec2d<SYS, true><<<grid, AT, 0, st>>>(g, H[l], dst, dt, c->sigma, c->status, R[l]);
+      else k_oe_rec2d<SYS, false><<<grid, AT, 0, st>>>(g, H[l], dst, dt, c->sigma, c->status, R[l]);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if ((e = cudaMemcpyAsync(dst, H[l], c->numel * sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
                cudaSuccess) {

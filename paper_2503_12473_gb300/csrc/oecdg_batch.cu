@@ -75,7 +75,11 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
   const int mesh = local / tiles, t = local - mesh * tiles;
   const int i = (t % in.tx) * 32 + (threadIdx.x & 31);
   const int j = (t / in.tx) * R + (threadIdx.x >> 5);
-  oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
+  // square cells: the isotropic variant, as the single-mesh launch chooses it
+  if (in.g.hx == in.g.hy)
+    oe_cell2d<SYS, BC, false, 0, true>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
+  else
+    oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
 }
 
 // avg and sigma per instance, mesh and field: grid (F, 2, n), fixed order
