@@ -178,3 +178,28 @@ def test_adjoint_refuses_generic_configurations():
     with pytest.raises(G.CdgError) as e:
         ctx.cdg_step_adjoint(u, u.clone(), torch.empty_like(u))
     assert e.value.status == G.CDG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["tiled_q2_riemann", "generic_p3_rk4", "tiled_q2_no_oe"])
+def test_step_graph_equals_step_2d(case):
+    """cdg_step_graph replays one captured step; results equal cdg_step_async
+    bit for bit on the tiled Q^2 kernels (with and without the OE step, whose
+    absence puts a copy node in the graph) and on the generic P^3 kernels with
+    RK4's extra stage buffers."""
+    from paper_2503_12473_gb300 import oecdg as G
+    if case == "generic_p3_rk4":
+        w = _wl(W.EULER, 3, W.BASIS_P, rk=4, nx=40, ny=20)
+        over = {}
+    else:
+        w = W.riemann_2d(n=48).resized(48, 36)
+        over = {"oe": 0} if case == "tiled_q2_no_oe" else {}
+    st = torch.cuda.Stream()
+    ctx = G.Context(G.desc_from_workload(w, **over), stream=st)
+    with torch.cuda.stream(st):
+        u0 = ctx.project(w.u0)
+        a = u0.clone()
+        b = u0.clone()
+    ctx.cdg_step_async(a, 0.0, 0.0, 5)
+    ctx.cdg_step_graph(b, 0.0, 0.0, 5)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert torch.equal(a, b)
