@@ -297,6 +297,13 @@ def run_ours(args, ws, rank, local):
                    "frac": BYTES_PER_CELL[kname] * cells / avg_s / 1e9 / hbm_peak,
                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     roof["kernel_share"] = {k: prof[k][0] / ms for k in ("stage", "oe")}
+    # the other hot kernel, same arithmetic
+    oname = "oe" if kname == "stage" else "stage"
+    oms, ocount = prof[oname]
+    if ocount and FLOPS_PER_CELL[oname] is not None:
+        o_ach = FLOPS_PER_CELL[oname] * cells / ((oms / ocount) * 1e-3) / 1e12
+        roof["other_kernel"] = {"kernel": f"k_{oname}2d", "avg_launch_ms": oms / ocount, "achieved": o_ach,
+                                "frac": o_ach / FP64_PEAK_TFLOPS, "flops_per_cell": FLOPS_PER_CELL[oname]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
