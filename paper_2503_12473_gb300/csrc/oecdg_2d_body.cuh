@@ -73,7 +73,14 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
       for (int a = 0; a < 3; ++a) R[f][b][a] = 0.0;
 
   const int oj0 = wrap_index<BC>(j + off, g.ny), oj1 = wrap_index<BC>(j + 1 + off, g.ny);
+// OECDG_STAGE_ROLL_SX=1 keeps the two halves apart (spill loads 1.6 -> 1.0 KB
+// per thread) but makes their quadrature constants run-time values: 2.5%
+// slower at 1024^2, so the halves stay unrolled by default.
+#if OECDG_STAGE_ROLL_SX
+#pragma unroll 1
+#else
 #pragma unroll
+#endif
   for (int sx = 0; sx < 2; ++sx) {
     const int oi = wrap_index<BC>(i + sx + off, g.nx);
     const double* c0 = uo + (long long)oj0 * g.nx + oi;
