@@ -203,3 +203,55 @@ def test_step_graph_equals_step_2d(case):
     ctx.cdg_step_graph(b, 0.0, 0.0, 5)
     assert ctx.cdg_check_status() == G.CDG_OK
     assert torch.equal(a, b)
+
+
+def _pk_eval(coef, k, g):
+    """Values of a P^k expansion (modes by total degree, then decreasing a) at
+    the tensor points g x g of every cell: coef [M, ny, nx] -> [ny, nx, q, q]."""
+    V = np.polynomial.legendre.legvander(g, k)  # [q, k+1]
+    out = 0.0
+    m = 0
+    for s in range(k + 1):
+        for a in range(s, -1, -1):
+            b = s - a
+            out = out + coef[m][:, :, None, None] * V[None, None, :, b][..., :, None] * V[None, None, :, a][..., None, :]
+            m += 1
+    return out
+
+
+def _l1_error(u, k, n, L, exact):
+    g, wq = np.polynomial.legendre.leggauss(k + 2)
+    v = _pk_eval(u[0, 0], k, g)  # primal mesh, first field
+    h = L / n
+    xs = (np.arange(n)[None, :, None, None] + 0.5 + 0.5 * g[None, None, None, :]) * h
+    ys = (np.arange(n)[:, None, None, None] + 0.5 + 0.5 * g[None, None, :, None]) * h
+    e = np.abs(v - exact(xs, ys))
+    return float(np.sum(e * np.outer(wq, wq)[None, None] / 4)) / (n * n)
+
+
+@pytest.mark.parametrize("case", ["euler_steady_wave", "advection"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_pk_orders_2d(case, k):
+    """The P^k scheme with its (k+1)-order RK method converges at order ~k+1
+    (the error estimate of Section 3.3; Tables 3 and 4): l1 error of the first
+    field over the primal cells at meshes 16^2 and 32^2, observed order > k + 0.5."""
+    errs = []
+    for n in (16, 32):
+        if case == "advection":
+            w = W.Workload("adv", 2, n, n, k, W.ADVECTION, W.PERIODIC, 0.0, 1.0, 0.0, 1.0, basis=W.BASIS_P,
+                           adv=(1.0, 1.0), cfl={1: 0.45, 2: 0.33, 3: 0.31}[k], rk=k + 1, u0=_sin2)
+            T, L = 0.25, 1.0
+            exact = lambda x, y: np.sin(np.pi * (x + y - 2 * T)) ** 2
+        else:
+            w = W.steady_wave_2d_workload(n, k, W.BASIS_P)
+            T, L = 0.5, 2.0
+            exact = lambda x, y: 1 + 0.2 * np.sin(np.pi * (x - y))
+        ctx = _ctx(w)
+        u = ctx.project(w.u0)
+        t = 0.0
+        while t < T:
+            ctx.cdg_step(u, t, T, 256)
+            t = ctx.cdg_get_time()
+        errs.append(_l1_error(u.cpu().numpy(), k, n, L, exact))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > k + 0.5, (errs, rate)
