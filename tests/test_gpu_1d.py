@@ -275,3 +275,42 @@ def test_step_graph_needs_own_stream():
     with pytest.raises(G.CdgError) as e:
         ctx.cdg_step_graph(u, 0.0, 0.0, 2)
     assert e.value.status == G.CDG_EINVAL
+
+
+@pytest.mark.parametrize("case", ["advection", "burgers"])
+@pytest.mark.parametrize("k", [1, 2])
+def test_pk_orders_1d(case, k):
+    """P^1 and P^2 with their (k+1)-order RK methods converge at order ~k+1
+    (Section 3.3; Tables 1 and 2): l1 error at the cell Gauss points of the
+    primal mesh, meshes 64 and 128, observed order > k + 0.5."""
+    errs = []
+    for n in (64, 128):
+        if case == "advection":
+            w = W.Workload("adv", 1, n, 1, k, W.ADVECTION, W.PERIODIC, 0.0, 1.0, adv=(1.0, 0.0),
+                           cfl={1: 0.45, 2: 0.33}[k], rk=k + 1, T=0.5,
+                           u0=lambda xy: np.sin(2 * np.pi * np.asarray(xy).reshape(len(xy), -1)[:, 0])[:, None])
+            ex = lambda x, t: np.sin(2 * np.pi * (x - t))
+            L = 1.0
+        else:
+            w = W.burgers_1d(n, k)
+            w = W.Workload(w.name, 1, n, 1, k, W.BURGERS, W.PERIODIC, w.ax, w.bx, cfl={1: 0.45, 2: 0.33}[k],
+                           rk=k + 1, T=0.6, u0=w.u0)
+            L = 2 * math.pi
+
+            def ex(x, t):
+                u = np.sin(x) + 0.5
+                for _ in range(60):
+                    u = u - (u - np.sin(x - u * t) - 0.5) / (1 + t * np.cos(x - u * t))
+                return u
+        ctx = _ctx(w)
+        u = ctx.project(w.u0)
+        t = 0.0
+        while t < w.T:
+            ctx.cdg_step(u, t, w.T, 512)
+            t = ctx.cdg_get_time()
+        g, wq = np.polynomial.legendre.leggauss(k + 2)
+        v = np.polynomial.legendre.legval(g, u.cpu().numpy()[0, 0, :, 0, :])  # [n, q]
+        x = (np.arange(n)[:, None] + 0.5 + 0.5 * g[None, :]) * (L / n)
+        errs.append(float(np.sum(np.abs(v - ex(x, t)) * wq / 2)) / n)
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > k + 0.5, (errs, rate)

@@ -283,3 +283,19 @@ def test_adjoint_full_size_vs_fd():
         fd = (L(u + eps * d) - L(u - eps * d)) / (2 * eps)
         an = (grad * d).sum().item()
         assert abs(an - fd) <= 2e-5 * abs(fd), (an, fd)
+
+
+def test_conservation_full_size_periodic():
+    """Conservation (Section 3.3): with periodic boundaries the total of every
+    conserved variable over both meshes, sum_K |K| u_K,00, is constant up to
+    round-off; the 256^2 vortex workload over 100 steps, in bench.py's launch
+    configuration."""
+    w = W.vortex_2d(n=256)
+    ctx, st = _bench_ctx(w)
+    with torch.cuda.stream(st):
+        u = ctx.project(w.u0)
+        tot0 = u[:, :, 0].sum(dim=(0, 2, 3)).cpu().numpy()
+        scale = u[:, :, 0].abs().sum(dim=(0, 2, 3)).cpu().numpy()
+        ctx.cdg_step(u, 0.0, 0.0, 100)
+        tot1 = u[:, :, 0].sum(dim=(0, 2, 3)).cpu().numpy()
+    assert np.all(np.abs(tot1 - tot0) <= 1e-12 * scale), (tot0, tot1)
