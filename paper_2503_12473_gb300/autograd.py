@@ -1,11 +1,13 @@
 """torch.autograd.Function over n OECDG time steps with sqrt(n) checkpoints.
 
 Forward: cdg_step_async one step at a time, keeping the state every `segment`
-steps (segment = ceil(sqrt(n)) by default).  Backward: for each segment, last
-first, recompute its steps from the checkpoint with cdg_step_record (which
-keeps each step's stages) and run cdg_step_adjoint_recorded through them in
-reverse.  Peak memory: sqrt(n) checkpoints plus 6 sqrt(n) states of records
-plus the library's adjoint scratch; every step is computed twice in all.  Every step and every adjoint runs in the
+steps (segment = ceil(sqrt(n)) by default); the steps of the last segment run
+as cdg_step_record (same states) and keep their records.  Backward: for each
+segment, last first, take or recompute its records (cdg_step_record from the
+segment's checkpoint) and run cdg_step_adjoint_recorded through them in
+reverse.  Peak memory: sqrt(n) checkpoints plus one segment of records (6
+states and the OE maxima per step) plus the library's adjoint scratch; every
+step outside the last segment is computed twice in all.  Every step and every adjoint runs in the
 CUDA library; this module only orders the calls.
 """
 from __future__ import annotations
@@ -20,14 +22,23 @@ class OECDGRollout(torch.autograd.Function):
     def forward(fctx, u0, context, nsteps: int, segment: int):
         u = u0.detach().contiguous().clone()
         chk = [u.clone()]
+        last_start = ((nsteps - 1) // segment) * segment if nsteps > 0 else 0
+        rec_numel = context.cdg_record_numel()
+        last_recs = []
         for s in range(nsteps):
-            context.cdg_step_async(u, 0.0, 0.0, 1)
+            if s >= last_start:
+                r = torch.empty(rec_numel, dtype=torch.float64, device=u.device)
+                context.cdg_step_record(u, r)
+                last_recs.append(r)
+            else:
+                context.cdg_step_async(u, 0.0, 0.0, 1)
             if (s + 1) % segment == 0 and s + 1 < nsteps:
                 chk.append(u.clone())
         fctx.context = context
         fctx.nsteps = nsteps
         fctx.segment = segment
         fctx.chk = chk
+        fctx.last_recs = last_recs
         return u
 
     @staticmethod
@@ -39,17 +50,22 @@ class OECDGRollout(torch.autograd.Function):
         for k in reversed(range(len(fctx.chk))):
             start = k * seg
             end = min(start + seg, n)
-            u = fctx.chk[k].clone()
-            recs = []
-            for _ in range(start, end):
-                r = torch.empty(rec_numel, dtype=torch.float64, device=u.device)
-                ctx.cdg_step_record(u, r)
-                recs.append(r)
+            if k == len(fctx.chk) - 1 and fctx.last_recs:
+                recs, fctx.last_recs = fctx.last_recs, None  # recorded by the forward pass
+            else:
+                u = fctx.chk[k].clone()
+                recs = []
+                for _ in range(start, end):
+                    r = torch.empty(rec_numel, dtype=torch.float64, device=u.device)
+                    ctx.cdg_step_record(u, r)
+                    recs.append(r)
+                del u
             for q in reversed(range(end - start)):
                 ctx.cdg_step_adjoint_recorded(recs[q], lam, nxt)
                 lam, nxt = nxt, lam
-            del recs, u
+            del recs
         fctx.chk = None
+        fctx.last_recs = None
         return lam, None, None, None
 
 
