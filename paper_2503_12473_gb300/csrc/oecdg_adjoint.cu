@@ -115,11 +115,18 @@ __global__ void __launch_bounds__(AT) k_rhs_vjp2d(Geo g, const double* __restric
   const long long self = (long long)mesh * F * 9 * P + (long long)jc * g.nx + ic;
   const int off = mesh == 0 ? -1 : 0;
 
-  // R_bar[f][b][a] = (2a+1)(2b+1)/16 * s * lam_h, read through the cache where
-  // needed (keeps 36 doubles out of the registers)
+  // R_bar[f][b][a] = (2a+1)(2b+1)/16 * s * lam_h, scaled once into this
+  // thread's column of shared memory (keeps 9 F doubles out of the registers
+  // and the scaling out of the FP64 pipe; each thread reads only its own column)
   const double sact = active ? s : 0.0;
   const double* lself = lamh + self;
-#define RB(f, b, a) ((2 * (a) + 1) * (2 * (b) + 1) / 16.0 * sact * __ldg(lself + ((f) * 9 + (b) * 3 + (a)) * P))
+  __shared__ double rbs[F * 9][AT];
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      rbs[f * 9 + q][threadIdx.x] = (2 * (q % 3) + 1) * (2 * (q / 3) + 1) / 16.0 * sact * __ldg(lself + (f * 9 + q) * P);
+#define RB(f, b, a) (rbs[(f) * 9 + (b) * 3 + (a)][threadIdx.x])
   double tm_acc = 0.0, t_acc = 0.0;
 #pragma unroll
   for (int f = 0; f < F; ++f)
