@@ -64,6 +64,16 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
   const double* us = u + (long long)mesh * F * 9 * P;
   const int off = mesh == 0 ? -1 : 0;
   const double kd = 0.5 * g.hy * inv_tm;  // dissipation scale inside A
+  // the dissipation weights w_qy kd P_b(eta) (b = 0, 1, 2) of every point row,
+  // uniform over the block: computed once into shared memory, so the points
+  // take them by broadcast instead of scaling every field value by kd
+  __shared__ double wk[2][3][3];
+  if (threadIdx.x < 18) {
+    const int sy = threadIdx.x / 9, qy = (threadIdx.x / 3) % 3, c = threadIdx.x % 3;
+    const double es = xs_self(sy, qy);
+    wk[sy][qy][c] = gwt(qy) * (c == 0 ? 1.0 : (c == 1 ? es : lp(2, es))) * kd;
+  }
+  __syncthreads();
   double R[F][3][3];
 #pragma unroll
   for (int f = 0; f < F; ++f)
@@ -162,12 +172,12 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
 #pragma unroll
           for (int f = 0; f < F; ++f) V[f] = fma(lp(2, eo), T[f][2], fma(eo, T[f][1], T[f][0]));
           flux_both<SYS>(g, V, f1, f2);
+          const double k0 = wk[sy][qy][0], k1 = wk[sy][qy][1], k2 = wk[sy][qy][2];
 #pragma unroll
           for (int f = 0; f < F; ++f) {
-            const double g0 = kd * V[f];
-            A[f][0] = fma(w, g0, A[f][0]);
-            A[f][1] = fma(w * es, g0, fma(w, f2[f], A[f][1]));
-            A[f][2] = fma(w * lp(2, es), g0, fma(w * dlp(2, es), f2[f], A[f][2]));
+            A[f][0] = fma(k0, V[f], A[f][0]);
+            A[f][1] = fma(k1, V[f], fma(w, f2[f], A[f][1]));
+            A[f][2] = fma(k2, V[f], fma(w * dlp(2, es), f2[f], A[f][2]));
             B[f][0] = fma(w, f1[f], B[f][0]);
             B[f][1] = fma(w * es, f1[f], B[f][1]);
             B[f][2] = fma(w * lp(2, es), f1[f], B[f][2]);
