@@ -47,10 +47,10 @@ HBM_FALLBACK_GBS = 6800.0
 # launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
 # kernels are branch-free and fully unrolled, so this is the arithmetic of the
 # algorithm as implemented.  Source: profiles/fp64_counts_euler2d_q2.md.
-FLOPS_PER_CELL = {"stage": 7327, "oe": 7113}
+FLOPS_PER_CELL = {"stage": 7327, "oe": 6921}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
 # once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 847, "oe": 807}
+TRAFFIC_PER_CELL = {"stage": 846, "oe": 808}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
 # (neighbour re-reads are L2 hits).

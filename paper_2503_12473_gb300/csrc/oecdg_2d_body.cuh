@@ -360,8 +360,8 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     double Sx0 = 0.0, Sx1 = 0.0, Sx2 = 0.0, Sy0 = 0.0, Sy1 = 0.0, Sy2 = 0.0;
     // Faces normal to direction n (0: x, 1: y), at reference coordinate s of K.
     // Along the face, K's trace and its normal derivatives of order 0, 1, 2 are
-    // Legendre series c0, c1, c2 in the tangential coordinate t; the overlapping
-    // cell's are o0, o1, o2 in its own tangential coordinate t' = t + dl,
+    // Legendre series c0, c1, 3 c2 in the tangential coordinate t; the
+    // overlapping cell's are o0, o1, 3 o2 in its own tangential coordinate t' = t + dl,
     // dl = 1 - 2 h (h = the half), re-expanded in t with
     //   P_1(t + dl) = P_1(t) + dl,  P_2(t + dl) = P_2(t) + 3 dl P_1(t) + 3/2.
     // The difference series (u_K - w) is then scaled to physical derivatives
@@ -381,7 +381,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           const double u2 = n == 0 ? u[t * 3 + 2] : u[6 + t];
           c0[t] = u0 + s * u1 + u2;
           c1[t] = fma(3.0 * s, u2, u1);
-          c2[t] = 3.0 * u2;
+          c2[t] = u2;  // the second normal derivative is 3 c2; the 3 is applied below
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -399,7 +399,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           // overlapping trace at its centre line (normal coordinate 0)
           const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
           const double* o1 = w1;
-          const double o2[3] = {3.0 * w2[0], 3.0 * w2[1], 3.0 * w2[2]};
+          const double* o2 = w2;  // (second normal derivative) / 3
           // difference series in K's tangential coordinate
           double e0[3], e1[3], e2[3];
           e0[2] = c0[2] - o0[2];
@@ -415,15 +415,18 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           // derivative of the value and of the normal derivative, second
           // tangential derivative (a constant on the half-face)
           double a0, a1, a2, b0, b1, b2, t0, t1, m0, m1, tt;
+          // (ISO: the factors 3 of the second normal and the mixed derivative
+          // go into the points' constant coefficients, see hn and hm below)
           if constexpr (ISO) {
             a0 = e1[0], a1 = e1[1], a2 = e1[2];
-            b0 = e2[0], b1 = e2[1], b2 = e2[2];
+            b0 = 3.0 * e2[0], b1 = e2[1], b2 = e2[2];
             t0 = e0[1], t1 = 3.0 * e0[2];
-            m0 = a1, m1 = 3.0 * a2;
+            m0 = a1, m1 = a2;
             tt = t1;
           } else {
+            const double dn2x3 = 3.0 * dn2;
             a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
-            b0 = dn2 * e2[0], b1 = dn2 * e2[1], b2 = dn2 * e2[2];
+            b0 = dn2x3 * e2[0], b1 = dn2x3 * e2[1], b2 = dn2x3 * e2[2];
             t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
             m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
             tt = 3.0 * dt2 * e0[2];
@@ -437,8 +440,9 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
             const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));   // u_K - w
             const double gn = fma(p2, a2, fma(ts, a1, a0));           // normal derivative
             const double gt = fma(ts, t1, t0);                        // tangential derivative
-            const double hn = fma(p2, b2, fma(ts, b1, b0));           // second normal
-            const double hm = fma(ts, m1, m0);                        // mixed
+            const double hn = ISO ? fma(3.0 * p2, b2, fma(3.0 * ts, b1, b0))  // second normal
+                                  : fma(p2, b2, fma(ts, b1, b0));
+            const double hm = ISO ? fma(3.0 * ts, m1, m0) : fma(ts, m1, m0);  // mixed
             S0 = fma(gwt(q), fabs(v), S0);
             S1 = fma(gwt(q), sqrt(fma(gn, gn, gt * gt)), S1);
             S2 = fma(gwt(q), sqrt(fma(hn, hn, fma(hm, hm, tt2))), S2);
