@@ -4,12 +4,17 @@
  * Peng, Wu, Yuan, arXiv:2503.12473.
  *
  * Scope of the CUDA path:
- *   - 2D: the tensor space Q^2, linear advection and the compressible Euler
- *     equations, forward Euler, SSP-RK2 or SSP-RK3;
+ *   - 2D: the tensor space Q^k or the total-degree space P^k, k = 1, 2 or 3,
+ *     linear advection, Burgers (f = g = u^2/2) and the compressible Euler
+ *     equations.  Q^2 with advection or Euler and forward Euler, SSP-RK2 or
+ *     SSP-RK3 runs on the tiled, sum-factorised kernels (the measured hot
+ *     path); every other 2D configuration, RK4 included, on the
+ *     degree-generic kernels;
  *   - 1D: P^k with k = 1, 2 or 3, linear advection, Burgers (f = u^2/2) and
- *     the 1D Euler equations, forward Euler, SSP-RK2, SSP-RK3 or the classical
+ *     the 1D Euler equations;
+ *   - time stepping: forward Euler, SSP-RK2, SSP-RK3 or the classical
  *     four-stage RK4 (written in Shu-Osher form, used for Table 2);
- * both with periodic or transmissive boundaries.
+ * all with periodic or transmissive boundaries.
  *
  * Conventions shared by every entry point
  *   - Every call returns a cdg_status; nothing throws, aborts or exits.
@@ -21,8 +26,10 @@
  *     shifted by (+hx/2, +hy/2); dual cell (i,j) is centred on primal vertex
  *     (i+1, j+1)); field = conserved variable (Euler 2D: rho, rho u, rho v, E;
  *     1D: rho, rho v, E; advection: u); mode = Legendre mode (a,b) of the
- *     unnormalised Legendre polynomials P_a(xi) P_b(eta) at index b*3 + a in 2D,
- *     a = 0..k in 1D.  j is absent (ny = 1) in 1D.
+ *     unnormalised Legendre polynomials P_a(xi) P_b(eta): Q^k at index
+ *     b*(k+1) + a, P^k ordered by total degree a+b and then by decreasing a
+ *     ((0,0), (1,0), (0,1), (2,0), (1,1), (0,2), ...); 1D: a = 0..k.  j is
+ *     absent (ny = 1) in 1D.
  *   - All calls are asynchronous on the context's stream unless stated.
  *   - tau and tau_max live in device memory owned by the context, so that a
  *     sequence of cdg_step_async calls can be captured in a CUDA graph.
@@ -57,12 +64,12 @@ enum { CDG_RK_EULER1 = 1, CDG_RK_SSP2 = 2, CDG_RK_SSP3 = 3, CDG_RK_RK4 = 4 };
 typedef struct {
   int dim;       /* 1 or 2 */
   int nx, ny;    /* primal cells per direction (ny is ignored when dim = 1) */
-  int k;         /* polynomial degree: 2 in 2D, 1..3 in 1D */
-  int basis;     /* CDG_BASIS_Q (1D: P^k = Q^k, either value accepted) */
-  int system;    /* CDG_ADVECTION, CDG_EULER, or (1D only) CDG_BURGERS */
+  int k;         /* polynomial degree: 1..3 */
+  int basis;     /* CDG_BASIS_Q or CDG_BASIS_P (1D: P^k = Q^k, either accepted) */
+  int system;    /* CDG_ADVECTION, CDG_BURGERS or CDG_EULER */
   int bc;        /* CDG_PERIODIC or CDG_TRANSMISSIVE on every side */
   int oe;        /* 1: apply the OE step F_tau after every RK stage */
-  int rk;        /* CDG_RK_EULER1, _SSP2, _SSP3, or (1D only) CDG_RK_RK4 */
+  int rk;        /* CDG_RK_EULER1, _SSP2, _SSP3 or _RK4 */
   int pad;
   double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
   double gamma;          /* ratio of specific heats (Euler) */
@@ -76,9 +83,7 @@ typedef struct cdg_ctx cdg_ctx;
  * `stream` (a cudaStream_t; NULL = the legacy default stream), on the current
  * device.  Allocates the geometry constants and the scratch buffers.
  * Errors: CDG_EINVAL (null pointers, sizes < 2, bad enums), CDG_EUNSUPPORTED
- * (2D: k != 2, basis P, Burgers or RK4; 1D: k outside 1..3), CDG_ENOMEM,
- * CDG_ECUDA.  On error *out is
- * NULL. */
+ * (k outside 1..3), CDG_ENOMEM, CDG_ECUDA.  On error *out is NULL. */
 cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out);
 
 /* Release a context (synchronises its stream first).  NULL is accepted. */
@@ -91,8 +96,8 @@ const char* cdg_last_error(const cdg_ctx* ctx);
 cdg_status cdg_state_numel(const cdg_ctx* ctx, size_t* numel);
 
 /* Sampling points of the projection-based initialisation (Section 3.3): on
- * every cell of both meshes, 3 x 3 (1D: k + 1) Gauss points on each of its 4
- * (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx] of (x, y) pairs (1D:
+ * every cell of both meshes, (k+1) x (k+1) (1D: k + 1) Gauss points on each
+ * of its 4 (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx] of (x, y) pairs (1D:
  * [mesh][i][sx][qx] of x).  With d_xy == NULL only *npts is set; otherwise
  * d_xy is a device array of npts * dim doubles. */
 cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts);
@@ -137,9 +142,9 @@ cdg_status cdg_rk_stage(cdg_ctx* ctx, int l, const double* d_un, const double* d
  * n in 1..4, d_terms a HOST array of n device state pointers, coef a host
  * array of n doubles.  Classical RK4's last stage is n = 4 with terms
  * (u^n, u^(1), u^(2), u^(3)), coef (-1/3, 1/3, 2/3, 1/3), ct = 1/6 and
- * d_ul = u^(3).  In 2D only the two-state form (n = 2, d_terms[1] == d_ul,
- * coef[1] == ct, or n = 1, d_terms[0] == d_ul, coef[0] == ct == 1) runs;
- * other forms return CDG_EUNSUPPORTED there.  d_out must not alias d_ul or
+ * d_ul = u^(3).  On the tiled 2D Q^2 path only the two-state form (n = 2,
+ * d_terms[1] == d_ul, coef[1] == ct, or n = 1, d_terms[0] == d_ul,
+ * coef[0] == ct == 1) runs; other forms return CDG_EUNSUPPORTED there.  d_out must not alias d_ul or
  * any term. */
 cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double* const* d_terms, const double* coef,
                           double ct, double* d_out);
@@ -199,9 +204,10 @@ cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
  * The three stages are recomputed from d_un.  d_un, d_lam_next: device states
  * (inputs); d_lam: device state (output, must not alias d_un; may alias
  * d_lam_next); d_gtau: NULL or 2 device doubles receiving the adjoints of tau
- * and tau_max of the step.  2D periodic SSP-RK3 only (CDG_EUNSUPPORTED
- * otherwise); with oe = 0 the OE paths are left out as in the forward step.  The first call allocates the adjoint scratch
- * (12 state-sized buffers) in the context.  Asynchronous. */
+ * and tau_max of the step.  2D periodic Q^2 advection or Euler with SSP-RK3
+ * only, i.e. the tiled path (CDG_EUNSUPPORTED otherwise); with oe = 0 the
+ * OE paths are left out as in the forward step.  The first call allocates the
+ * adjoint scratch (12 state-sized buffers) in the context.  Asynchronous. */
 cdg_status cdg_step_adjoint(cdg_ctx* ctx, const double* d_un, const double* d_lam_next, double* d_lam,
                             double* d_gtau);
 
@@ -243,7 +249,7 @@ cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, d
  * exits.  The paper has no counterpart: this is an interface for such callers,
  * not a step of the method.
  *
- * desc:   mesh description, same rules as cdg_init_mesh.
+ * desc:   mesh description, same rules as cdg_init_mesh within the scope below.
  * d_uh:   device state to damp (input, caller-owned); d_usig: device state
  *         (output, caller-owned, must not alias d_uh); both cdg_state_numel()
  *         doubles in the layout above.
@@ -261,7 +267,8 @@ cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, d
  * threads) race: the caller must order them.  Non-physical cell averages are
  * not reported by this entry point (their wave speed is taken as 0).
  * Errors: CDG_EINVAL (bad pointers or sizes, aliasing, tau < 0, mesh beyond the
- * limit), CDG_EUNSUPPORTED (as cdg_init_mesh), CDG_ECUDA. */
+ * limit), CDG_EUNSUPPORTED (k != 2, basis P in 2D, or Burgers: this entry
+ * point covers 2D Q^2 and 1D P^2 advection and Euler only), CDG_ECUDA. */
 cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const double* d_uh, double tau, double* d_usig,
                                void* stream);
 
