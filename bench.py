@@ -47,10 +47,10 @@ HBM_FALLBACK_GBS = 6800.0
 # launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
 # kernels are branch-free and fully unrolled, so this is the arithmetic of the
 # algorithm as implemented.  Source: profiles/fp64_counts_euler2d_q2.md.
-FLOPS_PER_CELL = {"stage": 7327, "oe": 6921}
+FLOPS_PER_CELL = {"stage": 7090, "oe": 6073}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
 # once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 846, "oe": 808}
+TRAFFIC_PER_CELL = {"stage": 925, "oe": 809}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
 # (neighbour re-reads are L2 hits).
@@ -321,15 +321,13 @@ def run_ours(args, ws, rank, local):
 
 
 # Executed FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes per cell of the
-# degree-generic 2D kernels, 2D Euler, periodic, one 512^2 launch each (the
-# state is larger than L2 for k >= 2); keys (k, basis).  Source:
-# profiles/fp64_counts_euler2d_generic.md.
-FLOPS_PER_CELL_2K = {(1, "P"): {"stage": 3409, "oe": 3091}, (2, "P"): {"stage": 9731, "oe": 8011},
-                     (3, "P"): {"stage": 22207, "oe": 17222}, (1, "Q"): {"stage": 3399, "oe": 3699},
-                     (3, "Q"): {"stage": 25070, "oe": 24750}}
-# None where the 512^2 state fits in L2 (k = 1, and P^2 at 100 MB): DRAM bytes
-# of that capture would not scale to a larger launch.
-TRAFFIC_PER_CELL_2K = {(3, "P"): {"stage": 1119, "oe": 952}, (3, "Q"): {"stage": 1495, "oe": 1498}}
+# degree-generic 2D kernels, 2D Euler, periodic, one 512^2 launch each; keys
+# (k, basis).  Empty: the counts in profiles/fp64_counts_euler2d_generic.md
+# were taken before these kernels moved to the seeded reciprocal and square
+# root (fewer flops per cell), so their lines report achieved and frac as null
+# until the kernels are counted again.
+FLOPS_PER_CELL_2K = {}
+TRAFFIC_PER_CELL_2K = {}
 
 
 def run_generic(args, ws, rank, local):

@@ -275,6 +275,20 @@ cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const double* d_uh, do
 /* Number of kernels launched by the context so far (host-side counter). */
 cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
 
+/* The FP64 reciprocal (op CDG_MATH_RCP) and square root (op CDG_MATH_SQRT)
+ * that the kernels use in their hot loops (1/rho of the Euler flux, the
+ * norms in the damping coefficients of Eq. (OEstep2D)), applied elementwise:
+ * d_y[i] = op(d_x[i]), i < n, so that they can be checked against correctly
+ * rounded results.  Not a step of the method.  Both are within about 1 ulp
+ * for 2^-1022 <= x <= 2^1022 (normal and positive, with a normal reciprocal);
+ * other inputs (zero, subnormal, negative, infinite, NaN) are outside their
+ * contract.  d_x, d_y: device arrays of n
+ * doubles (caller-owned; they may alias).  stream: a cudaStream_t (NULL =
+ * the legacy default stream); asynchronous.  n = 0 launches nothing.
+ * Errors: CDG_EINVAL (null pointers with n > 0, bad op), CDG_ECUDA. */
+enum { CDG_MATH_RCP = 0, CDG_MATH_SQRT = 1 };
+cdg_status cdg_math_eval(int op, const double* d_x, size_t n, double* d_y, void* stream);
+
 /* ------------------------------------------------------------- batches ---
  * Many independent 2D Euler Q^2 problems of uneven mesh sizes advanced together.
  * Not in the paper: each instance is exactly the single-mesh scheme above

@@ -431,7 +431,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
             m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
             tt = 3.0 * dt2 * e0[2];
           }
-          const double tt2 = tt * tt;
+          const double tt2 = fma(tt, tt, SQ_FLOOR);
           double S0 = 0.0, S1 = 0.0, S2 = 0.0;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -444,8 +444,8 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
                                   : fma(p2, b2, fma(ts, b1, b0));
             const double hm = ISO ? fma(3.0 * ts, m1, m0) : fma(ts, m1, m0);  // mixed
             S0 = fma(gwt(q), fabs(v), S0);
-            S1 = fma(gwt(q), sqrt(fma(gn, gn, gt * gt)), S1);
-            S2 = fma(gwt(q), sqrt(fma(hn, hn, fma(hm, hm, tt2))), S2);
+            S1 = fma(gwt(q), sqrt_pos(fma(gn, gn, fma(gt, gt, SQ_FLOOR))), S1);
+            S2 = fma(gwt(q), sqrt_pos(fma(hn, hn, fma(hm, hm, tt2))), S2);
           }
           if (n == 0) {
             Sx0 += S0;

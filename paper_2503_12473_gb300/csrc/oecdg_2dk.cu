@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
             const double t = h - 0.5 + 0.5 * gq;
 #pragma unroll
             for (int m = 0; m <= K; ++m) {
-              double ss = 0.0;
+              double ss = SQ_FLOOR;
 #pragma unroll
               for (int an = 0; an <= m; ++an) {
                 const int at = m - an;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
                 const double dv = v * sc;
                 ss = fma(dv, dv, ss);
               }
-              S[n][m] = fma(wq, sqrt(ss), S[n][m]);
+              S[n][m] = fma(wq, sqrt_pos(ss), S[n][m]);
             }
           }
         }

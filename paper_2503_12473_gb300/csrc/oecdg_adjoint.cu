@@ -38,7 +38,7 @@ constexpr int AT = 128;  // threads per block of the per-cell adjoint kernels
 // state w = (rho, m, n, E) (m = rho u, n = rho v).
 __device__ __forceinline__ void euler2_vjp(const double* w, const double* fb1, const double* fb2, double g,
                                            double* wb) {
-  const double r = 1.0 / w[0];
+  const double r = rcp_pos(w[0]);
   const double u = w[1] * r, v = w[2] * r;
   const double g1 = g - 1.0;
   const double p = g1 * (w[3] - 0.5 * (w[1] * u + w[2] * v));
@@ -598,8 +598,10 @@ __device__ __forceinline__ void oe_order_vjp(const Geo& g, const double* u, cons
             const double ts = xs_self(h, q), p2 = lp(2, ts);
             const double gn = fma(p2, a2, fma(ts, a1, a0));
             const double gt = fma(ts, t1, t0);
-            const double r1 = sqrt(fma(gn, gn, gt * gt));
-            const double k1 = r1 > 0.0 ? gwt(q) * Sb / r1 : 0.0;
+            // the forward kernel's floored norm (SQ_FLOOR): r1 > 0, and the
+            // gradient at a zero sum comes out as 0 through gn = gt = 0
+            const double r1 = sqrt_pos(fma(gn, gn, fma(gt, gt, SQ_FLOOR)));
+            const double k1 = gwt(q) * Sb * rcp_pos(r1);
             const double gnb = k1 * gn, gtb = k1 * gt;
             a0b += gnb;
             a1b += ts * gnb;
@@ -623,8 +625,8 @@ __device__ __forceinline__ void oe_order_vjp(const Geo& g, const double* u, cons
             const double ts = xs_self(h, q), p2 = lp(2, ts);
             const double hn = fma(p2, b2, fma(ts, b1, b0));
             const double hm = fma(ts, m1, m0);
-            const double r2 = sqrt(fma(hn, hn, fma(hm, hm, tt * tt)));
-            const double k2 = r2 > 0.0 ? gwt(q) * Sb / r2 : 0.0;
+            const double r2 = sqrt_pos(fma(hn, hn, fma(hm, hm, fma(tt, tt, SQ_FLOOR))));
+            const double k2 = gwt(q) * Sb * rcp_pos(r2);
             const double hnb = k2 * hn, hmb = k2 * hm;
             ttb += k2 * tt;
             b0b += hnb;

@@ -536,6 +536,28 @@ cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, d
   return CDG_OK;
 }
 
+}  // extern "C"
+
+template <int OP>
+__global__ void k_math_eval(const double* __restrict__ x, size_t n, double* __restrict__ y) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = OP == CDG_MATH_RCP ? rcp_pos(x[t]) : sqrt_pos(x[t]);
+}
+
+extern "C" {
+
+cdg_status cdg_math_eval(int op, const double* d_x, size_t n, double* d_y, void* stream) {
+  if (op != CDG_MATH_RCP && op != CDG_MATH_SQRT) return CDG_EINVAL;
+  if (n == 0) return CDG_OK;
+  if (!d_x || !d_y) return CDG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(need < 152 * 16 ? need : 152 * 16);
+  if (op == CDG_MATH_RCP) k_math_eval<CDG_MATH_RCP><<<blocks, 256, 0, st>>>(d_x, n, d_y);
+  else k_math_eval<CDG_MATH_SQRT><<<blocks, 256, 0, st>>>(d_x, n, d_y);
+  return cudaGetLastError() == cudaSuccess ? CDG_OK : CDG_ECUDA;
+}
+
 cdg_status cdg_step(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
   cdg_status s = cdg_step_async(ctx, d_u, t, T_end, nsteps);
   if (s != CDG_OK) return s;

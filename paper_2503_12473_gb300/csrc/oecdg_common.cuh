@@ -39,6 +39,36 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// FP64 reciprocal and square root of the hot loops.  The seed is the PTX
+// approximation computed from the upper 32 bits of the input
+// (rcp.approx.ftz.f64, rsqrt.approx.ftz.f64; their residuals e below measure
+// at most 2^-19.9 and 2^-19.0 on GB300); one higher-order Newton step then
+// multiplies it by the Taylor series, in the seed's residual e, of
+//   1/x      = y / (1 - e),          e = 1 - x y,
+//   sqrt(x)  = s / (1 - e)^(1/2),    s = x y,  e = 1 - s y,
+// cut after e^2.  The remainders, e^3 resp. 5e^3/16, stay below 2^-58
+// relative, so the results are within about 1 ulp (3 resp. 5 FP64
+// instructions after the seed).  Both need a normal, positive x with a normal
+// reciprocal (the seeds flush subnormals to zero); callers of sqrt_pos add
+// SQ_FLOOR into the sum of squares they pass, which makes a zero sum cost
+// nothing extra and moves a nonzero one by at most 1e-300.
+constexpr double SQ_FLOOR = 1e-300;
+
+__device__ __forceinline__ double rcp_pos(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);  // y (1 + e + e^2)
+}
+
+__device__ __forceinline__ double sqrt_pos(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double s = x * y;
+  const double e = fma(-s, y, 1.0);
+  return fma(s * e, fma(0.375, e, 0.5), s);  // s (1 + e/2 + 3e^2/8)
+}
+
 // Geometry and physics constants passed by value to every kernel.
 struct Geo {
   int nx, ny;
@@ -52,7 +82,7 @@ struct Geo {
 // 2D Euler flux components at a conserved state (rho, mx, my, E).
 struct Euler2 {
   __device__ static __forceinline__ void both(const double* w, double g, double* f1, double* f2) {
-    const double r = __drcp_rn(w[0]);
+    const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
     const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
     const double H = w[3] + p;
@@ -66,7 +96,7 @@ struct Euler2 {
     f2[3] = H * vy;
   }
   __device__ static __forceinline__ void fx(const double* w, double g, double* f1) {
-    const double r = __drcp_rn(w[0]);
+    const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
     const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
     f1[0] = w[1];
@@ -75,7 +105,7 @@ struct Euler2 {
     f1[3] = (w[3] + p) * vx;
   }
   __device__ static __forceinline__ void fy(const double* w, double g, double* f2) {
-    const double r = __drcp_rn(w[0]);
+    const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
     const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
     f2[0] = w[2];

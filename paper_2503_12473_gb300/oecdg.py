@@ -20,6 +20,7 @@ ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 RK_EULER1, RK_SSP2, RK_SSP3, RK_RK4 = 1, 2, 3, 4
+MATH_RCP, MATH_SQRT = 0, 1
 
 STATUS_NAMES = {0: "CDG_OK", 1: "CDG_EINVAL", 2: "CDG_ENOMEM", 3: "CDG_ECUDA", 4: "CDG_ENONPHYSICAL",
                 5: "CDG_ETIMEOUT", 6: "CDG_EUNSUPPORTED"}
@@ -32,7 +33,7 @@ EXPORTED = [
     "cdg_init_batch", "cdg_batch_free", "cdg_batch_last_error", "cdg_batch_step", "cdg_batch_check_status",
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
     "cdg_step_adjoint", "cdg_batch_set_rows", "cdg_record_numel", "cdg_step_record", "cdg_step_adjoint_recorded",
-    "cdg_rk_combine", "cdg_step_graph",
+    "cdg_rk_combine", "cdg_step_graph", "cdg_math_eval",
 ]
 
 
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = True):
                                   ctypes.POINTER(ctypes.c_longlong)]
     L.cdg_oe_damp_noalloc.restype = st
     L.cdg_oe_damp_noalloc.argtypes = [ctypes.POINTER(cdg_mesh_desc), vp, ctypes.c_double, vp, vp]
+    L.cdg_math_eval.restype = st
+    L.cdg_math_eval.argtypes = [ctypes.c_int, vp, sz, vp, vp]
     L.cdg_init_batch.restype = st
     L.cdg_init_batch.argtypes = [ctypes.POINTER(cdg_mesh_desc), ctypes.c_int, vp, ctypes.POINTER(vp)]
     L.cdg_batch_free.restype = st
@@ -224,6 +227,17 @@ def cdg_oe_damp_noalloc(desc: MeshDesc, d_uh, tau: float, d_usig, stream=None) -
     s = L.cdg_oe_damp_noalloc(ctypes.byref(cd), _ptr(d_uh), tau, _ptr(d_usig), ctypes.c_void_p(stream.cuda_stream))
     if s != CDG_OK:
         raise CdgError(s, "cdg_oe_damp_noalloc")
+
+
+def cdg_math_eval(op: int, d_x, d_y, stream=None) -> None:
+    """The kernels' FP64 reciprocal / square root applied elementwise (see include/oecdg.h)."""
+    import torch
+    L = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = L.cdg_math_eval(op, _ptr(d_x), d_x.numel(), _ptr(d_y), ctypes.c_void_p(stream.cuda_stream))
+    if s != CDG_OK:
+        raise CdgError(s, "cdg_math_eval")
 
 
 class Context:
