@@ -253,6 +253,110 @@ def test_delta_matches_1d_remark():
                 assert abs(delta[mesh, 0, i, m] - ref) <= 1e-12 * max(ref, 1e-300)
 
 
+def _euler_state_2d(p, seed):
+    """A physical 2D Euler modal state: averages rho in [0.9, 1.3], |m| < 0.4,
+    E in [2.4, 2.6] (so p > 0 at every average), small random higher modes."""
+    rng = np.random.default_rng(seed)
+    u = 0.05 * rng.standard_normal(p.shape)
+    sh = u.shape[:1] + u.shape[3:]
+    u[:, 0, 0] = rng.uniform(0.9, 1.3, sh)
+    u[:, 1, 0] = rng.uniform(-0.4, 0.4, sh)
+    u[:, 2, 0] = rng.uniform(-0.4, 0.4, sh)
+    u[:, 3, 0] = rng.uniform(2.4, 2.6, sh)
+    return u
+
+
+@pytest.mark.parametrize("system,k,basis", [(O.ADVECTION, 2, O.BASIS_Q), (O.ADVECTION, 2, O.BASIS_P),
+                                            (O.ADVECTION, 3, O.BASIS_Q), (O.ADVECTION, 1, O.BASIS_P),
+                                            (O.EULER, 2, O.BASIS_Q), (O.EULER, 3, O.BASIS_P)])
+def test_delta_2d_from_its_definition(system, k, basis):
+    """The damping coefficient delta_K^m of Section 2.2 on a 2D mesh, evaluated
+    here term by term from its definition with numpy Legendre derivatives:
+        delta_K^m = sum_e beta_e (2m+1) h_e^(m-1) / ((2k-1) m! sigma |e|)
+                    int_e ( sum_{|alpha|=m} (d^alpha (u_K - w))^2 )^(1/2) ds,
+    with K's own trace u_K, the other mesh's solution w located by point, the
+    integral by (k+1) Gauss points on each half of e (the halves lie in two
+    cells of the other mesh), h_e the cell width normal to e, sigma the max of
+    |u - avg| over the cells' Gauss points, beta_e the normal wave speed at K's
+    average, and for Euler the max over the four fields.  Non-square cells and a
+    velocity with unequal components keep the x and y parts apart; every
+    multi-index (a, m - a) enters once, the mixed ones included."""
+    nx, ny, Lx, Ly, ax, ay = 5, 4, 1.25, 0.6, 0.7, -1.3
+    p = O.Problem(dim=2, nx=nx, ny=ny, k=k, basis=basis, system=system, bc=O.PERIODIC, bx=Lx, by=Ly,
+                  adv_x=ax, adv_y=ay, gamma=1.4)
+    u = _rand_state(p, 41) if system == O.ADVECTION else _euler_state_2d(p, 41)
+    delta, sigma, avg, st = O.oe_coefficients(p, u)
+    assert st == 0
+    hx, hy = Lx / nx, Ly / ny
+    md = ND.modes(2, k, basis == O.BASIS_Q)
+    F = u.shape[1]
+    g, wg = np.polynomial.legendre.leggauss(k + 1)
+
+    def centre(mesh, i, j):  # dual cell (i, j) is centred on primal vertex (i + 1, j + 1)
+        return (i + 0.5 + 0.5 * mesh) * hx, (j + 0.5 + 0.5 * mesh) * hy
+
+    def poly(mesh, f, i, j, xi, eta, dx, dy):
+        c = u[mesh, f, :, j % ny, i % nx]
+        v = sum(c[q] * ND.leg(a, xi, dx) * ND.leg(b, eta, dy) for q, (a, b) in enumerate(md))
+        return v * (2.0 / hx) ** dx * (2.0 / hy) ** dy
+
+    def at_point(mesh, f, x, y, dx, dy):
+        i = int(np.floor(x / hx - 0.5 * mesh))
+        j = int(np.floor(y / hy - 0.5 * mesh))
+        xc, yc = centre(mesh, i, j)
+        return poly(mesh, f, i, j, (x - xc) / (0.5 * hx), (y - yc) / (0.5 * hy), dx, dy)
+
+    # sigma: max over every cell's (k+1)^2 Gauss points of |u - avg|, avg = mean cell average
+    sg = np.zeros((2, F))
+    for mesh in range(2):
+        for f in range(F):
+            av = u[mesh, f, 0].mean()
+            vals = [poly(mesh, f, i, j, x, y, 0, 0) for j in range(ny) for i in range(nx) for x in g for y in g]
+            sg[mesh, f] = np.max(np.abs(np.array(vals) - av))
+    np.testing.assert_allclose(sigma, sg, rtol=1e-13, atol=0)
+
+    def speeds(mesh, i, j):
+        if system == O.ADVECTION:
+            return abs(ax), abs(ay)
+        r, mx, my, E = u[mesh, :, 0, j, i]
+        pr = 0.4 * (E - 0.5 * (mx * mx + my * my) / r)
+        c = math.sqrt(1.4 * pr / r)
+        return abs(mx / r) + c, abs(my / r) + c
+
+    worst = 0.0
+    for mesh in range(2):
+        for j in range(ny):
+            for i in range(nx):
+                xc, yc = centre(mesh, i, j)
+                bx, by = speeds(mesh, i, j)
+                for m in range(k + 1):
+                    best = 0.0
+                    for f in range(F):
+                        tot = 0.0
+                        # faces normal to x (length hy, h_e = hx) and to y (length hx, h_e = hy)
+                        for nrm, side in [(0, -1), (0, 1), (1, -1), (1, 1)]:
+                            beta, he, le = (bx, hx, hy) if nrm == 0 else (by, hy, hx)
+                            integral = 0.0
+                            for half in (-1, 1):
+                                for q in range(k + 1):
+                                    t = (half + g[q]) / 2.0  # Gauss node of this half, on [-1, 1]
+                                    xi, eta = (side, t) if nrm == 0 else (t, side)
+                                    x, y = xc + 0.5 * hx * xi, yc + 0.5 * hy * eta
+                                    ss = 0.0
+                                    for dx in range(m + 1):
+                                        dy = m - dx
+                                        d = poly(mesh, f, i, j, xi, eta, dx, dy) - at_point(1 - mesh, f, x, y, dx, dy)
+                                        ss += d * d
+                                    integral += (0.25 * le * wg[q]) * math.sqrt(ss)
+                            tot += beta * (2 * m + 1) * he ** (m - 1) / ((2 * k - 1) * math.factorial(m)) \
+                                * integral / le
+                        best = max(best, tot / sg[mesh, f])
+                    got = delta[mesh, j, i, m]
+                    assert abs(got - best) <= 1e-12 * best, (mesh, i, j, m, got, best)
+                    worst = max(worst, abs(got - best) / best)
+    assert worst < 1e-12
+
+
 def test_k0_forward_euler_is_staggered_lax_friedrichs():
     """With k = 0, one forward-Euler step and tau = tau_max, Eq. (eq:1D_H) reduces
     to the first-order staggered Lax-Friedrichs scheme
