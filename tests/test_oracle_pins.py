@@ -617,6 +617,31 @@ def test_euler_steady_wave_converges():
     assert all(r > 2.8 for r in rates), (errs, rates)
 
 
+def test_euler_vortex_converges_to_the_translated_vortex():
+    """The isentropic vortex (exact solution of the 2D Euler equations, checked
+    by the test below) advected for t = 0.25 on [0, 10]^2: the oracle's Q^2
+    SSP-RK3 density converges to the translated vortex at order near k + 1.
+    Unlike the steady wave, the vortex has pressure and velocity gradients in
+    both directions, so every term of both flux components matters."""
+    T, errs = 0.25, []
+    g, w = np.polynomial.legendre.leggauss(3)
+    XI, ETA = np.meshgrid(g, g)
+    WW = np.outer(w, w).ravel() / 4
+    for n in (16, 32):
+        p = O.Problem(dim=2, nx=n, ny=n, k=2, system=O.EULER, bc=O.PERIODIC, bx=10.0, by=10.0, cfl=0.33)
+        u, t, _, st = O.advance(p, O.project_fn(p, W.isentropic_vortex()), 0.0, T)
+        assert st == 0 and abs(t - T) < 1e-12
+        v = O.eval_cells(p, u, 0, XI.ravel(), ETA.ravel())[..., 0]  # [ny, nx, points]
+        h = 10.0 / n
+        xs = (np.arange(n)[None, :, None] + 0.5 + 0.5 * XI.ravel()[None, None, :]) * h
+        ys = (np.arange(n)[:, None, None] + 0.5 + 0.5 * ETA.ravel()[None, None, :]) * h
+        xs, ys = np.broadcast_arrays(xs, ys)
+        rho = W.isentropic_vortex(t=T)(np.stack([xs.ravel(), ys.ravel()], 1))[:, 0].reshape(xs.shape)
+        errs.append(np.sum(np.abs(v - rho) * WW) / n ** 2)
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 3.0 and errs[1] < 1e-4, (errs, rate)
+
+
 def test_vortex_initial_data_is_a_translating_solution():
     """The isentropic vortex formula used for the adjoint workload solves the 2D
     Euler equations exactly: its space-time finite-difference residual shrinks
