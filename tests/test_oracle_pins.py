@@ -357,6 +357,43 @@ def test_delta_2d_from_its_definition(system, k, basis):
     assert worst < 1e-12
 
 
+@pytest.mark.parametrize("dim,system", [(2, O.EULER), (2, O.ADVECTION), (1, O.EULER), (1, O.BURGERS)])
+def test_tau_max_matches_section4(dim, system):
+    """The time step of Section 4: 2D tau = C / (beta_x / h_x + beta_y / h_y)
+    with beta_x, beta_y the largest x- and y-wave speeds, each maximised on its
+    own; 1D tau = C h / beta.  The wave speeds are taken at the cell averages of
+    both meshes (Euler |v_n| + c, advection |a_n|, Burgers |u|)."""
+    nx, ny, Lx, Ly, C = 5, 4, 1.25, 0.6, 0.3
+    p = O.Problem(dim=dim, nx=nx, ny=ny, k=2, system=system, bc=O.PERIODIC, bx=Lx, by=Ly, adv_x=0.7,
+                  adv_y=-1.3, gamma=1.4, cfl=C)
+    if system == O.EULER and dim == 2:
+        u = _euler_state_2d(p, 43)
+    elif system == O.EULER:
+        rng = np.random.default_rng(43)
+        u = 0.05 * rng.standard_normal(p.shape)
+        u[:, 0, 0] = rng.uniform(0.9, 1.3, u[:, 0, 0].shape)
+        u[:, 1, 0] = rng.uniform(-0.4, 0.4, u[:, 0, 0].shape)
+        u[:, 2, 0] = rng.uniform(2.4, 2.6, u[:, 0, 0].shape)
+    else:
+        u = _rand_state(p, 43)
+    got, st = O.tau_max(p, u)
+    assert st == 0
+    a = u[:, :, 0]  # cell averages [mesh, field, ny, nx]
+    if system == O.EULER:
+        r = a[:, 0]
+        vel = [a[:, 1 + d] / r for d in range(dim)]
+        E = a[:, dim + 1]
+        pr = 0.4 * (E - 0.5 * r * sum(v * v for v in vel))
+        c = np.sqrt(1.4 * pr / r)
+        beta = [np.max(np.abs(v) + c) for v in vel]
+    elif system == O.ADVECTION:
+        beta = [0.7, 1.3][:dim]
+    else:
+        beta = [np.max(np.abs(a[:, 0]))]
+    want = C / (beta[0] / (Lx / nx) + beta[1] / (Ly / ny)) if dim == 2 else C * (Lx / nx) / beta[0]
+    assert abs(got - want) <= 1e-14 * want, (got, want)
+
+
 def test_k0_forward_euler_is_staggered_lax_friedrichs():
     """With k = 0, one forward-Euler step and tau = tau_max, Eq. (eq:1D_H) reduces
     to the first-order staggered Lax-Friedrichs scheme
