@@ -268,7 +268,8 @@ def _euler_state_2d(p, seed):
 
 @pytest.mark.parametrize("system,k,basis", [(O.ADVECTION, 2, O.BASIS_Q), (O.ADVECTION, 2, O.BASIS_P),
                                             (O.ADVECTION, 3, O.BASIS_Q), (O.ADVECTION, 1, O.BASIS_P),
-                                            (O.EULER, 2, O.BASIS_Q), (O.EULER, 3, O.BASIS_P)])
+                                            (O.EULER, 2, O.BASIS_Q), (O.EULER, 3, O.BASIS_P),
+                                            (O.BURGERS, 2, O.BASIS_P)])
 def test_delta_2d_from_its_definition(system, k, basis):
     """The damping coefficient delta_K^m of Section 2.2 on a 2D mesh, evaluated
     here term by term from its definition with numpy Legendre derivatives:
@@ -278,13 +279,14 @@ def test_delta_2d_from_its_definition(system, k, basis):
     integral by (k+1) Gauss points on each half of e (the halves lie in two
     cells of the other mesh), h_e the cell width normal to e, sigma the max of
     |u - avg| over the cells' Gauss points, beta_e the normal wave speed at K's
-    average, and for Euler the max over the four fields.  Non-square cells and a
+    average (2D Burgers, f = g = u^2/2: |u| on both face directions), and for
+    Euler the max over the four fields.  Non-square cells and a
     velocity with unequal components keep the x and y parts apart; every
     multi-index (a, m - a) enters once, the mixed ones included."""
     nx, ny, Lx, Ly, ax, ay = 5, 4, 1.25, 0.6, 0.7, -1.3
     p = O.Problem(dim=2, nx=nx, ny=ny, k=k, basis=basis, system=system, bc=O.PERIODIC, bx=Lx, by=Ly,
                   adv_x=ax, adv_y=ay, gamma=1.4)
-    u = _rand_state(p, 41) if system == O.ADVECTION else _euler_state_2d(p, 41)
+    u = _euler_state_2d(p, 41) if system == O.EULER else _rand_state(p, 41)
     delta, sigma, avg, st = O.oe_coefficients(p, u)
     assert st == 0
     hx, hy = Lx / nx, Ly / ny
@@ -318,6 +320,8 @@ def test_delta_2d_from_its_definition(system, k, basis):
     def speeds(mesh, i, j):
         if system == O.ADVECTION:
             return abs(ax), abs(ay)
+        if system == O.BURGERS:
+            return abs(u[mesh, 0, 0, j, i]), abs(u[mesh, 0, 0, j, i])
         r, mx, my, E = u[mesh, :, 0, j, i]
         pr = 0.4 * (E - 0.5 * (mx * mx + my * my) / r)
         c = math.sqrt(1.4 * pr / r)
@@ -504,19 +508,20 @@ def test_transpose_symmetry():
     np.testing.assert_allclose(tr(a), b, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("system,oe", [(O.ADVECTION, 1), (O.EULER, 0)])
+@pytest.mark.parametrize("system,oe", [(O.ADVECTION, 1), (O.EULER, 0), (O.BURGERS, 0)])
 @pytest.mark.parametrize("axis", [0, 1])
 def test_2d_reduces_to_1d(system, oe, axis):
     """Data that depend on one coordinate only: the 2D Q^k scheme (Eq. (eq:2D_H))
     reproduces the 1D scheme (Eq. (eq:1D_H)) on the modes of that direction.
     For advection along that axis the OE step reduces as well (the other
-    faces see zero wave speed); for Euler the test runs without OE because the
-    other faces carry the sound speed."""
+    faces see zero wave speed); for Euler and 2D Burgers (f = g = u^2/2, whose
+    y-flux of x-only data cancels between the volume and the two faces) the
+    test runs without OE because the other faces carry a wave speed."""
     n, k = 8, 2
     p1 = O.Problem(dim=1, nx=n, k=k, system=system, bc=O.PERIODIC, oe=oe, adv_x=1.0, cfl=0.2)
     p2 = O.Problem(dim=2, nx=n, ny=n, k=k, system=system, bc=O.PERIODIC, oe=oe, cfl=0.2,
                    adv_x=1.0 if axis == 0 else 0.0, adv_y=0.0 if axis == 0 else 1.0)
-    if system == O.ADVECTION:
+    if system != O.EULER:
         u1 = O.project_fn(p1, lambda xy: (np.sin(2 * np.pi * xy[:, 0]) + 0.3 * (xy[:, 0] > 0.4))[:, None])
     else:
         u1 = O.project_fn(p1, lambda xy: W.prim_to_cons_1d(1 + 0.3 * np.sin(2 * np.pi * xy[:, 0]),
@@ -526,7 +531,7 @@ def test_2d_reduces_to_1d(system, oe, axis):
         # mode (q, 0) in x, or (0, q) in y
         m2 = q if axis == 0 else q * (k + 1)
         for f1 in range(p1.nfields):
-            f2 = f1 if system == O.ADVECTION else [0, 1 + axis, 3][f1]
+            f2 = f1 if system != O.EULER else [0, 1 + axis, 3][f1]
             u2[:, f2, m2] = u1[:, f1, q, 0, :][:, None, :] if axis == 0 else u1[:, f1, q, 0, :][:, :, None]
     # same (tau, tau_max) on both sides: the 2D CFL formula also sees the other
     # direction's wave speed (the sound speed, for Euler)
@@ -538,7 +543,7 @@ def test_2d_reduces_to_1d(system, oe, axis):
     for q in range(k + 1):
         m2 = q if axis == 0 else q * (k + 1)
         for f1 in range(p1.nfields):
-            f2 = f1 if system == O.ADVECTION else [0, 1 + axis, 3][f1]
+            f2 = f1 if system != O.EULER else [0, 1 + axis, 3][f1]
             got = a2[:, f2, m2]
             ref = a1[:, f1, q, 0, :][:, None, :] if axis == 0 else a1[:, f1, q, 0, :][:, :, None]
             np.testing.assert_allclose(got, np.broadcast_to(ref, got.shape), rtol=0, atol=1e-12)
