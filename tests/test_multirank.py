@@ -48,3 +48,31 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
         steps, warmup, n = 1, 0, 64
     bench.run_reference(A(), ws=2, rank=1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys):
+    """Rank 0 of the reference arm prints one JSON line carrying the keys of
+    the bench contract, with the oracle's own rate as value, cpu_baseline and
+    e2e (no host-device copies)."""
+    import json
+
+    import bench
+
+    class A:
+        steps, warmup, n = 1, 0, 1024
+    bench.run_reference(A(), ws=1, rank=0)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] and d["config"]["nx"] == 1024
