@@ -39,3 +39,44 @@ def test_no_cpu_fallback_in_product_path():
     for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(path).read()
         assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", src, flags=re.M), path
+
+
+def _desc(**kw):
+    from paper_2503_12473_gb300 import oecdg as G
+    base = dict(dim=2, nx=8, ny=8, k=2, basis=G.BASIS_Q, system=G.EULER, bc=G.PERIODIC, oe=1, rk=G.RK_SSP3,
+                ax=0.0, bx=1.0, ay=0.0, by=1.0, gamma=1.4, adv_x=1.0, adv_y=1.0, cfl=0.3)
+    base.update(kw)
+    return G.MeshDesc(**base).c()
+
+
+def test_host_argument_checks_need_no_gpu():
+    """Descriptor and argument checks run on the host before any CUDA call, so
+    they answer here without a GPU: cdg_init_mesh, cdg_oe_damp_noalloc and
+    cdg_math_eval return CDG_EINVAL / CDG_EUNSUPPORTED as include/oecdg.h states."""
+    from paper_2503_12473_gb300 import oecdg as G
+    L = G.load()
+    EINVAL, EUNS = G.CDG_EINVAL, G.CDG_EUNSUPPORTED
+    cases = [(dict(dim=3), EINVAL), (dict(nx=1), EINVAL), (dict(ny=1), EINVAL), (dict(bc=2), EINVAL),
+             (dict(system=3), EINVAL), (dict(rk=0), EINVAL), (dict(rk=5), EINVAL), (dict(basis=2), EINVAL),
+             (dict(k=0), EUNS), (dict(k=4), EUNS), (dict(bx=0.0), EINVAL), (dict(by=-1.0), EINVAL),
+             (dict(cfl=0.0), EINVAL), (dict(gamma=1.0), EINVAL), (dict(nx=65536, ny=65536), EINVAL)]
+    for kw, want in cases:
+        d = _desc(**kw)
+        h = ctypes.c_void_p(1)
+        assert L.cdg_init_mesh(ctypes.byref(d), None, ctypes.byref(h)) == want, kw
+        assert h.value is None, kw  # *out is NULL on error
+    assert L.cdg_init_mesh(None, None, ctypes.byref(ctypes.c_void_p())) == EINVAL
+    assert L.cdg_init_mesh(ctypes.byref(_desc()), None, None) == EINVAL
+    # the no-alloc OE: its own scope (Q^2 / P^2 advection and Euler) and scratch limit
+    a, b = ctypes.c_void_p(16), ctypes.c_void_p(32)  # never dereferenced: the checks fail first
+    for kw, want in [(dict(k=3), EUNS), (dict(basis=G.BASIS_P), EUNS), (dict(system=G.BURGERS), EUNS),
+                     (dict(nx=1), EINVAL), (dict(nx=2048, ny=2048), EINVAL)]:
+        assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc(**kw)), a, 0.1, b, None) == want, kw
+    assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), a, -1.0, b, None) == EINVAL
+    assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), a, 0.1, a, None) == EINVAL  # aliasing
+    assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), None, 0.1, b, None) == EINVAL
+    # the kernels' reciprocal / square root entry: bad op, null pointers, and n = 0 (no launch)
+    assert L.cdg_math_eval(7, a, 4, b, None) == EINVAL
+    assert L.cdg_math_eval(G.MATH_SQRT, None, 4, b, None) == EINVAL
+    assert L.cdg_math_eval(G.MATH_RCP, None, 0, None, None) == G.CDG_OK
+    assert L.cdg_last_error(None) == b""
