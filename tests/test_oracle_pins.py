@@ -398,6 +398,34 @@ def test_tau_max_matches_section4(dim, system):
     assert abs(got - want) <= 1e-14 * want, (got, want)
 
 
+@pytest.mark.parametrize("rk", [1, 2, 3, 4])
+@pytest.mark.parametrize("dim,k,basis", [(1, 3, O.BASIS_Q), (2, 2, O.BASIS_Q), (2, 3, O.BASIS_P)])
+def test_rk_step_is_its_stability_polynomial(rk, dim, k, basis):
+    """For a linear semi-discretisation (advection, OE off) an explicit s-stage
+    method of order s <= 4 advances u by the truncated exponential
+    sum_{j <= s} (tau L)^j / j! -- forward Euler, SSP-RK2, SSP-RK3 and classical
+    RK4 of Eq. (eq:RKCDG) and Section 4.  The right side applies the oracle's
+    RHS j times (L at the step's tau_max), so a wrong stage coefficient of any
+    of the four methods shows here."""
+    p = O.Problem(dim=dim, nx=6, ny=5, k=k, basis=basis, system=O.ADVECTION, bc=O.PERIODIC, oe=0, rk=rk,
+                  bx=1.0, by=0.8, adv_x=0.7, adv_y=-1.3, cfl=0.3)
+    u = _rand_state(p, 47)
+    tm, _ = O.tau_max(p, u)
+    tau = 0.7 * tm
+    ref = u.copy()
+    term = u.copy()
+    for j in range(1, rk + 1):
+        term = O.rhs(p, term, tm) * (tau / j)
+        ref = ref + term
+    got, st = O.step_tau(p, u, tau, tm)
+    assert st == 0
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err < 1e-13, err
+    # and the method is not of a higher order: the next Taylor term is visible
+    nxt = O.rhs(p, term, tm) * (tau / (rk + 1))
+    assert np.abs(nxt).max() / np.abs(ref).max() > 1e-6
+
+
 def test_k0_forward_euler_is_staggered_lax_friedrichs():
     """With k = 0, one forward-Euler step and tau = tau_max, Eq. (eq:1D_H) reduces
     to the first-order staggered Lax-Friedrichs scheme
