@@ -538,16 +538,25 @@ def test_transpose_symmetry():
 
 @pytest.mark.parametrize("system,oe", [(O.ADVECTION, 1), (O.EULER, 0), (O.BURGERS, 0)])
 @pytest.mark.parametrize("axis", [0, 1])
-def test_2d_reduces_to_1d(system, oe, axis):
-    """Data that depend on one coordinate only: the 2D Q^k scheme (Eq. (eq:2D_H))
+@pytest.mark.parametrize("basis", [O.BASIS_Q, O.BASIS_P])
+def test_2d_reduces_to_1d(system, oe, axis, basis):
+    """Data that depend on one coordinate only: the 2D scheme (Eq. (eq:2D_H))
     reproduces the 1D scheme (Eq. (eq:1D_H)) on the modes of that direction.
     For advection along that axis the OE step reduces as well (the other
     faces see zero wave speed); for Euler and 2D Burgers (f = g = u^2/2, whose
     y-flux of x-only data cancels between the volume and the two faces) the
-    test runs without OE because the other faces carry a wave speed."""
+    test runs without OE because the other faces carry a wave speed.  Both 2D
+    spaces: Q^k (mode (a, b) at b (k+1) + a) and P^k (by total degree s, then
+    decreasing a: (q, 0) at q (q+1)/2, (0, q) at q (q+1)/2 + q)."""
     n, k = 8, 2
+
+    def m2(q):
+        if basis == O.BASIS_Q:
+            return q if axis == 0 else q * (k + 1)
+        return q * (q + 1) // 2 + (0 if axis == 0 else q)
+
     p1 = O.Problem(dim=1, nx=n, k=k, system=system, bc=O.PERIODIC, oe=oe, adv_x=1.0, cfl=0.2)
-    p2 = O.Problem(dim=2, nx=n, ny=n, k=k, system=system, bc=O.PERIODIC, oe=oe, cfl=0.2,
+    p2 = O.Problem(dim=2, nx=n, ny=n, k=k, basis=basis, system=system, bc=O.PERIODIC, oe=oe, cfl=0.2,
                    adv_x=1.0 if axis == 0 else 0.0, adv_y=0.0 if axis == 0 else 1.0)
     if system != O.EULER:
         u1 = O.project_fn(p1, lambda xy: (np.sin(2 * np.pi * xy[:, 0]) + 0.3 * (xy[:, 0] > 0.4))[:, None])
@@ -557,10 +566,9 @@ def test_2d_reduces_to_1d(system, oe, axis):
     u2 = p2.zeros()
     for q in range(k + 1):
         # mode (q, 0) in x, or (0, q) in y
-        m2 = q if axis == 0 else q * (k + 1)
         for f1 in range(p1.nfields):
             f2 = f1 if system != O.EULER else [0, 1 + axis, 3][f1]
-            u2[:, f2, m2] = u1[:, f1, q, 0, :][:, None, :] if axis == 0 else u1[:, f1, q, 0, :][:, :, None]
+            u2[:, f2, m2(q)] = u1[:, f1, q, 0, :][:, None, :] if axis == 0 else u1[:, f1, q, 0, :][:, :, None]
     # same (tau, tau_max) on both sides: the 2D CFL formula also sees the other
     # direction's wave speed (the sound speed, for Euler)
     tm, _ = O.tau_max(p1, u1)
@@ -569,10 +577,9 @@ def test_2d_reduces_to_1d(system, oe, axis):
         a1, s1 = O.step_tau(p1, a1, tm, tm)
         a2, s2 = O.step_tau(p2, a2, tm, tm)
     for q in range(k + 1):
-        m2 = q if axis == 0 else q * (k + 1)
         for f1 in range(p1.nfields):
             f2 = f1 if system != O.EULER else [0, 1 + axis, 3][f1]
-            got = a2[:, f2, m2]
+            got = a2[:, f2, m2(q)]
             ref = a1[:, f1, q, 0, :][:, None, :] if axis == 0 else a1[:, f1, q, 0, :][:, :, None]
             np.testing.assert_allclose(got, np.broadcast_to(ref, got.shape), rtol=0, atol=1e-12)
 
