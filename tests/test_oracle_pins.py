@@ -540,7 +540,8 @@ def test_transpose_symmetry():
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("basis", [O.BASIS_Q, O.BASIS_P])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_2d_reduces_to_1d(system, oe, axis, basis, k):
+@pytest.mark.parametrize("bc", [O.PERIODIC, O.TRANSMISSIVE])
+def test_2d_reduces_to_1d(system, oe, axis, basis, k, bc):
     """Data that depend on one coordinate only: the 2D scheme (Eq. (eq:2D_H))
     reproduces the 1D scheme (Eq. (eq:1D_H)) on the modes of that direction.
     For advection along that axis the OE step reduces as well (the other
@@ -548,7 +549,9 @@ def test_2d_reduces_to_1d(system, oe, axis, basis, k):
     y-flux of x-only data cancels between the volume and the two faces) the
     test runs without OE because the other faces carry a wave speed.  Both 2D
     spaces: Q^k (mode (a, b) at b (k+1) + a) and P^k (by total degree s, then
-    decreasing a: (q, 0) at q (q+1)/2, (0, q) at q (q+1)/2 + q)."""
+    decreasing a: (q, 0) at q (q+1)/2, (0, q) at q (q+1)/2 + q).  Periodic and
+    transmissive meshes: the 2D closure (a copy of the nearest stored cell per
+    direction) keeps one-dimensional data one-dimensional and matches 1D."""
     n = 8
 
     def m2(q):
@@ -556,8 +559,8 @@ def test_2d_reduces_to_1d(system, oe, axis, basis, k):
             return q if axis == 0 else q * (k + 1)
         return q * (q + 1) // 2 + (0 if axis == 0 else q)
 
-    p1 = O.Problem(dim=1, nx=n, k=k, system=system, bc=O.PERIODIC, oe=oe, adv_x=1.0, cfl=0.2)
-    p2 = O.Problem(dim=2, nx=n, ny=n, k=k, basis=basis, system=system, bc=O.PERIODIC, oe=oe, cfl=0.2,
+    p1 = O.Problem(dim=1, nx=n, k=k, system=system, bc=bc, oe=oe, adv_x=1.0, cfl=0.2)
+    p2 = O.Problem(dim=2, nx=n, ny=n, k=k, basis=basis, system=system, bc=bc, oe=oe, cfl=0.2,
                    adv_x=1.0 if axis == 0 else 0.0, adv_y=0.0 if axis == 0 else 1.0)
     if system != O.EULER:
         u1 = O.project_fn(p1, lambda xy: (np.sin(2 * np.pi * xy[:, 0]) + 0.3 * (xy[:, 0] > 0.4))[:, None])
