@@ -1002,6 +1002,7 @@ static cdg_status adj_alloc(cdg_ctx* c) {
                ADJ_WBLK * 4 + 2 + 3 * (size_t)24 * g.plane;
   double* p = nullptr;
   if (cudaMalloc((void**)&p, tot * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();  // clear the failed allocation: later launch checks must not see it
     free(a);
     return CDG_ENOMEM;
   }

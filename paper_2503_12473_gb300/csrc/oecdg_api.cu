@@ -131,6 +131,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   *out = c;
   return CDG_OK;
 nomem:
+  (void)cudaGetLastError();  // clear the failed allocation: later launch checks must not see it
   cdg_free(c);
   return CDG_ENOMEM;
 }

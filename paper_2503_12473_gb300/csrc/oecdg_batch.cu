@@ -311,6 +311,7 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
   if (cudaMalloc((void**)&B->pool, total * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&B->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
       cudaMalloc((void**)&B->status, sizeof(int)) != cudaSuccess) {
+    (void)cudaGetLastError();  // clear the failed allocation: later launch checks must not see it
     cdg_batch_free(B);
     return CDG_ENOMEM;
   }
