@@ -216,9 +216,10 @@ cdg_status cdg_step_adjoint(cdg_ctx* ctx, const double* d_un, const double* d_la
  * the adjoint of that step needs -- u^n, the three stages' u_h and the first
  * two stages' u_sigma, (tau, tau_max), and per cell and stage the OE step's
  * damping coefficients with the field that gives each of them and that field's
- * face sums: cdg_record_numel() doubles (6 states + 2 + 3 x 24 x cells).  cdg_step_adjoint_recorded then runs the backward pass
- * without recomputing the stages: d_lam = (du^{n+1}/du^n)^T d_lam_next, as
- * cdg_step_adjoint.  Same scope and scratch as cdg_step_adjoint. */
+ * face sums: cdg_record_numel() doubles (6 states + 2 + 3 x 24 x cells).
+ * cdg_step_adjoint_recorded then runs the backward pass without recomputing
+ * the stages: d_lam = (du^{n+1}/du^n)^T d_lam_next, as cdg_step_adjoint.  Same
+ * scope and scratch as cdg_step_adjoint. */
 cdg_status cdg_record_numel(const cdg_ctx* ctx, size_t* numel);
 cdg_status cdg_step_record(cdg_ctx* ctx, double* d_u, double* d_rec);
 cdg_status cdg_step_adjoint_recorded(cdg_ctx* ctx, const double* d_rec, const double* d_lam_next, double* d_lam,
