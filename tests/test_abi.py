@@ -80,3 +80,21 @@ def test_host_argument_checks_need_no_gpu():
     assert L.cdg_math_eval(G.MATH_SQRT, None, 4, b, None) == EINVAL
     assert L.cdg_math_eval(G.MATH_RCP, None, 0, None, None) == G.CDG_OK
     assert L.cdg_last_error(None) == b""
+
+
+def test_binding_fails_loudly_without_device_memory():
+    """No CPU fallback: the binding refuses host tensors and arrays, and on a
+    machine without a GPU creating a context raises instead of running
+    anything on the CPU."""
+    import numpy as np
+    import pytest
+    import torch
+    from paper_2503_12473_gb300 import oecdg as G
+    assert G._ptr(None) is None
+    with pytest.raises(ValueError):
+        G._ptr(torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        G._ptr(np.zeros(3))
+    if not torch.cuda.is_available():
+        with pytest.raises(Exception):
+            G.Context(G.MeshDesc(nx=8, ny=8))
