@@ -46,7 +46,8 @@ HBM_FALLBACK_GBS = 6800.0
 # the two hot kernels, counted from the executed FP64 instructions of one
 # launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
 # kernels are branch-free and fully unrolled, so this is the arithmetic of the
-# algorithm as implemented.  Source: profiles/fp64_counts_euler2d_q2.md.
+# algorithm as implemented.  Source: an ncu capture of the FP64 instruction
+# counters of one 512^2 launch of each kernel.
 FLOPS_PER_CELL = {"stage": 7090, "oe": 6073}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
 # once a kernel changes after the capture.
@@ -322,10 +323,10 @@ def run_ours(args, ws, rank, local):
 
 # Executed FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes per cell of the
 # degree-generic 2D kernels, 2D Euler, periodic, one 512^2 launch each; keys
-# (k, basis).  Empty: the counts in profiles/fp64_counts_euler2d_generic.md
-# were taken before these kernels moved to the seeded reciprocal and square
-# root (fewer flops per cell), so their lines report achieved and frac as null
-# until the kernels are counted again.
+# (k, basis).  Empty: the earlier ncu counts were taken before these kernels
+# moved to the seeded reciprocal and square root (fewer flops per cell), so
+# their lines report achieved and frac as null until the kernels are counted
+# again.
 FLOPS_PER_CELL_2K = {}
 TRAFFIC_PER_CELL_2K = {}
 

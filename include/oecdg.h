@@ -254,7 +254,7 @@ cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, d
  * d_uh:   device state to damp (input, caller-owned); d_usig: device state
  *         (output, caller-owned, must not alias d_uh); both cdg_state_numel()
  *         doubles in the layout above.
- * tau:    damping time (>= 0), the t_hat = tau of Eq. (OEstep2D).
+ * tau:    damping time (>= 0), as the context's tau in cdg_oe_damp.
  * stream: a cudaStream_t (NULL = the legacy default stream); asynchronous.
  * Limit:  the partials need 2 * ceil(cells per mesh / 256) * fields * 3
  *         doubles of the 131,008 available: at most 1,397,248 cells per mesh
@@ -263,7 +263,9 @@ cdg_status cdg_profile_end(cdg_ctx* ctx, double* ms_stage, long long* n_stage, d
  *         CDG_EINVAL without launching anything.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the one array and overwrites or clears
+ * any stream capture.  The address is kept for the life of the process, so do
+ * not use this entry point on a device after cudaDeviceReset (or any other
+ * teardown of its primary context) in the same process.  Every call shares the one array and overwrites or clears
  * what it uses, so calls that overlap on the GPU (two streams, or two host
  * threads) race: the caller must order them.  Non-physical cell averages are
  * not reported by this entry point (their wave speed is taken as 0).
@@ -280,10 +282,13 @@ cdg_status cdg_launch_count(const cdg_ctx* ctx, long long* count);
  * that the kernels use in their hot loops (1/rho of the Euler flux, the
  * norms in the damping coefficients of Eq. (OEstep2D)), applied elementwise:
  * d_y[i] = op(d_x[i]), i < n, so that they can be checked against correctly
- * rounded results.  Not a step of the method.  Both are within about 1 ulp
- * for 2^-1022 <= x <= 2^1022 (normal and positive, with a normal reciprocal);
- * other inputs (zero, subnormal, negative, infinite, NaN) are outside their
- * contract.  d_x, d_y: device arrays of n
+ * rounded results.  Not a step of the method.  The reciprocal is within 1 ulp
+ * for 2^-1022 <= |x| <= 2^1022, either sign (point densities can be negative
+ * in discontinuous runs), and odd: rcp(-x) = -rcp(x); the square root within
+ * 1 ulp for 2^-1022 <= x <= 2^1022.  Outside those ranges (zero, subnormal,
+ * infinite, NaN, or a negative square-root argument) the results are not
+ * specified (the reciprocal gives NaN for zero and subnormal |x|).  d_x, d_y:
+ * device arrays of n
  * doubles (caller-owned; they may alias).  stream: a cudaStream_t (NULL =
  * the legacy default stream); asynchronous.  n = 0 launches nothing.
  * Errors: CDG_EINVAL (null pointers with n > 0, bad op), CDG_ECUDA. */

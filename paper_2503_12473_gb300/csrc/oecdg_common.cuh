@@ -42,16 +42,26 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 // FP64 reciprocal and square root of the hot loops.  The seed is the PTX
 // approximation computed from the upper 32 bits of the input
 // (rcp.approx.ftz.f64, rsqrt.approx.ftz.f64; their residuals e below measure
-// at most 2^-19.9 and 2^-19.0 on GB300); one higher-order Newton step then
+// at most 2^-19.9 and 2^-19.0 on GB300); one higher-order Newton-Raphson step
+// (the iterations for division and square root in J.-M. Muller et al.,
+// Handbook of Floating-Point Arithmetic, Birkhauser, 2nd ed. 2018) then
 // multiplies it by the Taylor series, in the seed's residual e, of
 //   1/x      = y / (1 - e),          e = 1 - x y,
 //   sqrt(x)  = s / (1 - e)^(1/2),    s = x y,  e = 1 - s y,
 // cut after e^2.  The remainders, e^3 resp. 5e^3/16, stay below 2^-58
 // relative, so the results are within about 1 ulp (3 resp. 5 FP64
-// instructions after the seed).  Both need a normal, positive x with a normal
-// reciprocal (the seeds flush subnormals to zero); callers of sqrt_pos add
-// SQ_FLOOR into the sum of squares they pass, which makes a zero sum cost
-// nothing extra and moves a nonzero one by at most 1e-300.
+// instructions after the seed).
+//   rcp_pos: within 1 ulp for every normal x of EITHER sign whose reciprocal
+//     is normal, 2^-1022 <= |x| <= 2^1022 (the seed and the correction are odd
+//     in x, so rcp_pos(-x) = -rcp_pos(x) exactly).  The Euler flux calls it on
+//     point densities, which can be negative in discontinuous runs (the paper
+//     uses no limiter for them); |x| < 2^-1022 (zero or subnormal) or infinite
+//     x give NaN where IEEE division gives +-inf or 0, and |x| > 2^1022 gives 0
+//     where it gives a subnormal: a point density that small leaves the flux
+//     undefined either way.
+//   sqrt_pos: within 1 ulp for normal x > 0; callers add SQ_FLOOR into the
+//     sum of squares they pass, which makes a zero sum cost nothing extra and
+//     moves a nonzero one by at most 1e-300.
 constexpr double SQ_FLOOR = 1e-300;
 
 __device__ __forceinline__ double rcp_pos(double x) {

@@ -79,7 +79,9 @@ __global__ void __launch_bounds__(NA_BLOCK) k_sigma_partials_na(Geo g, const dou
   }
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device, looked up once
+// and kept for the life of the process (a device reset would invalidate it;
+// the header rules that use out).
 static cudaError_t noalloc_scratch(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -218,13 +218,33 @@ def desc_from_workload(w, **over) -> MeshDesc:
 
 
 def cdg_oe_damp_noalloc(desc: MeshDesc, d_uh, tau: float, d_usig, stream=None) -> None:
-    """The context-free, allocation-free OE step (see include/oecdg.h)."""
+    """The context-free, allocation-free OE step (see include/oecdg.h).
+
+    The C entry point takes its sizes from `desc` alone and its scratch from
+    the current device, so the binding checks, before anything is launched,
+    that both tensors hold exactly the state of `desc` and sit on one device,
+    and makes the call with that device current on its current stream (or on
+    `stream`, which must belong to the same device)."""
     import torch
+    numel = 1
+    for n in desc.shape:
+        numel *= n
+    for name, t in (("d_uh", d_uh), ("d_usig", d_usig)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: expected a torch.Tensor")
+        if t.numel() != numel:
+            raise ValueError(f"{name} has {t.numel()} elements; the mesh description needs {numel}")
+    if d_uh.device != d_usig.device:
+        raise ValueError(f"d_uh is on {d_uh.device} and d_usig on {d_usig.device}: both must be on one device")
+    pu, ps = _ptr(d_uh), _ptr(d_usig)
     L = load()
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    cd = desc.c()
-    s = L.cdg_oe_damp_noalloc(ctypes.byref(cd), _ptr(d_uh), tau, _ptr(d_usig), ctypes.c_void_p(stream.cuda_stream))
+    with torch.cuda.device(d_uh.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(d_uh.device)
+        elif stream.device != d_uh.device:
+            raise ValueError(f"stream is on {stream.device}, the states on {d_uh.device}")
+        cd = desc.c()
+        s = L.cdg_oe_damp_noalloc(ctypes.byref(cd), pu, tau, ps, ctypes.c_void_p(stream.cuda_stream))
     if s != CDG_OK:
         raise CdgError(s, "cdg_oe_damp_noalloc")
 

@@ -72,6 +72,11 @@ def test_host_argument_checks_need_no_gpu():
     for kw, want in [(dict(k=3), EUNS), (dict(basis=G.BASIS_P), EUNS), (dict(system=G.BURGERS), EUNS),
                      (dict(nx=1), EINVAL), (dict(nx=2048, ny=2048), EINVAL)]:
         assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc(**kw)), a, 0.1, b, None) == want, kw
+    # the scratch limit, one block of 256 cells past it (the largest accepted
+    # meshes run on the GPU in test_zz_no_alloc.py)
+    for kw in (dict(nx=512, ny=2730),  # 2D Euler: 5,460 blocks; 5,458 fit
+               dict(dim=1, nx=5589504 + 1, system=G.ADVECTION)):  # 1D advection: 21,835; 21,834 fit
+        assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc(**kw)), a, 0.1, b, None) == EINVAL, kw
     assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), a, -1.0, b, None) == EINVAL
     assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), a, 0.1, a, None) == EINVAL  # aliasing
     assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc()), None, 0.1, b, None) == EINVAL
@@ -98,3 +103,24 @@ def test_binding_fails_loudly_without_device_memory():
     if not torch.cuda.is_available():
         with pytest.raises(Exception):
             G.Context(G.MeshDesc(nx=8, ny=8))
+
+
+def test_noalloc_binding_checks_sizes_and_devices_before_any_launch():
+    """cdg_oe_damp_noalloc takes its sizes from the mesh description alone, so
+    the binding refuses, before loading or launching anything, tensors whose
+    element count is not the description's state size, and states that are
+    not device memory."""
+    import pytest
+    import torch
+    from paper_2503_12473_gb300 import oecdg as G
+    desc = G.MeshDesc(dim=2, nx=8, ny=6)
+    n = 2 * 4 * 9 * 8 * 6
+    good = torch.zeros(n, dtype=torch.float64)
+    short = torch.zeros(n - 1, dtype=torch.float64)
+    for a, b in ((short, good), (good, short)):
+        with pytest.raises(ValueError, match="elements"):
+            G.cdg_oe_damp_noalloc(desc, a, 1e-3, b)
+    with pytest.raises(ValueError):  # host memory, right size: refused, no CPU fallback
+        G.cdg_oe_damp_noalloc(desc, good, 1e-3, good.clone())
+    with pytest.raises(TypeError):
+        G.cdg_oe_damp_noalloc(desc, good.numpy(), 1e-3, good)

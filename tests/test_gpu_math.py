@@ -50,6 +50,31 @@ def test_math_eval_within_one_ulp(op):
     assert torch.equal(xd, yd)
 
 
+def test_reciprocal_of_negative_and_tiny_densities():
+    """The Euler flux takes 1/rho at every quadrature point, and without a
+    limiter point densities of discontinuous runs can be negative or tiny
+    (cell averages stay positive).  The reciprocal keeps its 1-ulp bound
+    there: negative inputs over the whole normal range, magnitudes down to
+    2^-1022, and exact oddness rcp(-x) = -rcp(x)."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    rng = np.random.default_rng(23)
+    pos = np.concatenate([_inputs(1 << 19, 29),
+                          np.ldexp(rng.uniform(1.0, 2.0, 1 << 16), rng.integers(-1022, -1000, 1 << 16)),
+                          np.exp(rng.uniform(np.log(1e-12), np.log(1e-3), 1 << 16))])
+    x = np.concatenate([-pos, pos])
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    G.cdg_math_eval(G.MATH_RCP, xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    assert np.isfinite(y).all()
+    u = _ulps(y, 1.0 / x)
+    assert u.max() <= 1, (u.max(), x[np.argmax(u)])
+    n = len(pos)
+    assert np.array_equal(y[:n], -y[n:])
+
+
 def test_math_eval_rejects_bad_arguments():
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required for -m gpu tests")
