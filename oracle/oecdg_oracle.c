@@ -180,8 +180,11 @@ static void cell_centre(const orc_problem* p, int mesh, int i, int j, double* xc
 /* Map an unwrapped cell index to a stored one: periodic wrap, or the
  * transmissive ghost convention (ghost cell := copy of the nearest stored cell,
  * every mode copied; corners by composition).  The paper does not say how the
- * dual mesh is closed at an outflow boundary: the transmissive branch is a
- * convention, parity unpinned. */
+ * dual mesh is closed at an outflow boundary.  Pinned where an outflow
+ * boundary is fixed by the physics: while the flow beside the boundary is
+ * uniform in the normal direction, a run equals the run on an enlarged domain
+ * cell for cell (tests/test_oracle_transmissive.py); the zeroth-order
+ * extrapolation beyond that is a convention. */
 static int store_index(const orc_problem* p, int iu, int n) {
   if (p->bc == ORC_PERIODIC) return ((iu % n) + n) % n;
   return iu < 0 ? 0 : (iu >= n ? n - 1 : iu);
