@@ -45,16 +45,19 @@ HBM_FALLBACK_GBS = 6800.0
 # Algorithmic FP64 flops per cell (one primal or dual cell, 2D Euler Q^2) of
 # the two hot kernels, counted from the executed FP64 instructions of one
 # launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
-# kernels are branch-free and fully unrolled, so this is the arithmetic of the
-# algorithm as implemented.  Source: an ncu capture of the FP64 instruction
-# counters of one 512^2 launch of each kernel.
-FLOPS_PER_CELL = {"stage": 7090, "oe": 6073}
-# DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture); None
-# once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 925, "oe": 809}
+# kernels are fully unrolled, so this is the arithmetic of the algorithm as
+# implemented.  The stage kernel's first stage (no u^n term) does 6,942 per
+# cell, the other two 7,014: the figure is their mean over a step.  Source: an
+# ncu capture of the FP64 instruction counters of the three stage and three OE
+# launches of one 512^2 step.
+FLOPS_PER_CELL = {"stage": 6990, "oe": 6065}
+# DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture,
+# mean over the step's launches); None once a kernel changes after the capture.
+TRAFFIC_PER_CELL = {"stage": 822, "oe": 500}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
-# (neighbour re-reads are L2 hits).
+# (neighbour re-reads, of both meshes, are L2 hits: the two meshes' blocks of a
+# tile run side by side).
 BYTES_PER_CELL = {"stage": (36 + 24 + 36) * 8, "oe": (36 + 36) * 8}
 
 

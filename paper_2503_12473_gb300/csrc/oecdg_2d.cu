@@ -27,11 +27,11 @@ __global__ void __launch_bounds__(NT, OECDG_STAGE_MINB) k_stage2d(Geo g, const d
                                                 const double* __restrict__ dt, double ca, double cb,
                                                 double* __restrict__ partials) {
   constexpr int F = Fields<SYS>::F;
-  const int mesh = blockIdx.z;
-  const long long nblk = (long long)gridDim.x * gridDim.y;
-  const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  const int mesh = blockIdx.x & 1, bx = blockIdx.x >> 1, tx = gridDim.x >> 1;
+  const long long nblk = (long long)tx * gridDim.y;
+  const long long blk = (long long)blockIdx.y * tx + bx;
   stage_cell2d<SYS, BC, MODE>(g, uin, un, out, dt, ca, cb, partials + (mesh * nblk + blk) * F * 3, mesh,
-                              blockIdx.x * TX + (threadIdx.x % TX), blockIdx.y * TY + (threadIdx.x / TX));
+                              bx * TX + (threadIdx.x % TX), blockIdx.y * TY + (threadIdx.x / TX));
 }
 
 // Fixed-order reduction of the block partials: avg and sigma per mesh and
@@ -72,8 +72,9 @@ template <int SYS, int BC, bool WRITE_DELTA, bool ISO>
 __global__ void __launch_bounds__(NT, OECDG_OE_MINB) k_oe2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                              const double* __restrict__ dt, const double* __restrict__ sigma,
                                              double* __restrict__ delta_out, int* __restrict__ status) {
-  oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.z,
-                                  blockIdx.x * TX + (threadIdx.x % TX), blockIdx.y * TY + (threadIdx.x / TX));
+  oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.x & 1,
+                                          (blockIdx.x >> 1) * TX + (threadIdx.x % TX),
+                                          blockIdx.y * TY + (threadIdx.x / TX));
 }
 
 // ------------------------------------------------------------- time step --
@@ -200,12 +201,13 @@ __global__ void k_project2d(Geo g, const double* __restrict__ vals, double* __re
 
 // ----------------------------------------------------------------- launch --
 
-static inline dim3 tile_grid(const Geo& g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 2); }
+// The two meshes' blocks of a tile are adjacent in launch order (mesh =
+// blockIdx.x & 1), so the cells a block reads from the other mesh were just
+// read by its partner block and are still in L2: each state is read from DRAM
+// about once per launch instead of once per mesh.
+static inline dim3 tile_grid(const Geo& g) { return dim3(2 * ((g.nx + TX - 1) / TX), (g.ny + TY - 1) / TY, 1); }
 
-long long partial_blocks_2d(const Geo& g) {
-  const dim3 gr = tile_grid(g);
-  return (long long)gr.x * gr.y;
-}
+long long partial_blocks_2d(const Geo& g) { return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY); }
 
 template <int SYS, int BC>
 static cudaError_t stage2d_t(const Geo& g, int mode, const double* uin, const double* un, double* out, const double* dt,

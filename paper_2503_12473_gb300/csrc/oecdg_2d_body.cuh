@@ -10,6 +10,8 @@
 // xi' = xi + 1 - 2 sx (the overlapping cell's centre lies on K's face).
 #pragma once
 
+#include <climits>
+
 #include "oecdg_common.cuh"
 
 namespace oecdg {
@@ -55,13 +57,26 @@ __device__ __forceinline__ void flux_y(const Geo& g, const double* V, double* f2
 // half-faces normal to x are two more columns (xi = -1, +1), the half-faces
 // normal to y two more points of every column (eta = -1, +1).
 // R holds 16 hx hy / ((2a+1)(2b+1)) times the bracket, indexed [f][b][a].
-template <int SYS, int BC>
+template <int F>
+struct RhsAcc {
+  double r[F][3][3];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) r[f][b][a] = 0.0;
+  }
+  __device__ __forceinline__ double& at(int f, int b, int a) { return r[f][b][a]; }
+};
+
+template <int SYS, int BC, class Acc>
 __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restrict__ u, int mesh, int i, int j,
-                                           double inv_tm, double (&L)[Fields<SYS>::F][9]) {
+                                           double inv_tm, Acc& R) {
   constexpr int F = Fields<SYS>::F;
   const long long P = g.plane;
   const double* uo = u + (long long)(1 - mesh) * F * 9 * P;
-  const double* us = u + (long long)mesh * F * 9 * P;
   const int off = mesh == 0 ? -1 : 0;
   const double kd = 0.5 * g.hy * inv_tm;  // dissipation scale inside A
   // the dissipation weights w_qy kd P_b(eta) (b = 0, 1, 2) of every point row,
@@ -74,13 +89,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
     wk[sy][qy][c] = gwt(qy) * (c == 0 ? 1.0 : (c == 1 ? es : lp(2, es))) * kd;
   }
   __syncthreads();
-  double R[F][3][3];
-#pragma unroll
-  for (int f = 0; f < F; ++f)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) R[f][b][a] = 0.0;
+  R.zero();
 
   const int oj0 = wrap_index<BC>(j + off, g.ny), oj1 = wrap_index<BC>(j + 1 + off, g.ny);
 // OECDG_STAGE_ROLL_SX=1 keeps the two halves apart (spill loads 1.6 -> 1.0 KB
@@ -134,13 +143,13 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
         for (int b = 0; b < 3; ++b) {
           const double v = sc * Bf[f][b];
           if (sx) {
-            R[f][b][0] -= v;
-            R[f][b][1] -= v;
-            R[f][b][2] -= v;
+            R.at(f, b, 0) -= v;
+            R.at(f, b, 1) -= v;
+            R.at(f, b, 2) -= v;
           } else {
-            R[f][b][0] += v;
-            R[f][b][1] -= v;
-            R[f][b][2] += v;
+            R.at(f, b, 0) += v;
+            R.at(f, b, 1) -= v;
+            R.at(f, b, 2) += v;
           }
         }
     }
@@ -211,23 +220,57 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
       for (int f = 0; f < F; ++f)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          R[f][b][0] = fma(wa, A[f][b], R[f][b][0]);
-          R[f][b][1] = fma(wa1, A[f][b], fma(wb, B[f][b], R[f][b][1]));
-          R[f][b][2] = fma(wa2, A[f][b], fma(wb2, B[f][b], R[f][b][2]));
+          R.at(f, b, 0) = fma(wa, A[f][b], R.at(f, b, 0));
+          R.at(f, b, 1) = fma(wa1, A[f][b], fma(wb, B[f][b], R.at(f, b, 1)));
+          R.at(f, b, 2) = fma(wa2, A[f][b], fma(wb2, B[f][b], R.at(f, b, 2)));
         }
     }
   }
-  // L_ab = (2a+1)(2b+1)/16 R_ab - u_ab / tau_max  (the -(1/tau_max) int u_K phi term
-  // is exact through the diagonal mass matrix)
-  const double* cs = us + (long long)j * g.nx + i;
+  // The caller forms L_ab = (2a+1)(2b+1)/16 R_ab - u_ab / tau_max: the
+  // -(1/tau_max) int u_K phi term is exact through the diagonal mass matrix.
+}
+
+// Order-preserving map of a double to a signed 64-bit key and back: the
+// sigma extrema are taken on the integer pipes, which leaves the FP64 pipe
+// (the kernel's bound) to the arithmetic.  For every non-NaN x, y:
+// x < y <=> key(x) < key(y) (-0 sorts just below +0).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// block reduction of (sum, key max, key min): result valid in thread 0
+__device__ __forceinline__ void block_reduce_sum_keys(double& s, long long& kx, long long& kn, double* sh) {
+  const unsigned full = 0xffffffffu;
 #pragma unroll
-  for (int f = 0; f < F; ++f)
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(full, s, o);
+    kx = max(kx, __shfl_down_sync(full, kx, o));
+    kn = min(kn, __shfl_down_sync(full, kn, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  long long* shk = (long long*)(sh + 32);
+  __syncthreads();
+  if (lane == 0) {
+    sh[warp] = s;
+    shk[warp] = kx;
+    shk[32 + warp] = kn;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < nw ? sh[lane] : 0.0;
+    kx = lane < nw ? shk[lane] : LLONG_MIN;
+    kn = lane < nw ? shk[32 + lane] : LLONG_MAX;
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        L[f][b * 3 + a] = fma((2 * a + 1) * (2 * b + 1) / 16.0, R[f][b][a],
-                              -inv_tm * __ldg(cs + (f * 9 + b * 3 + a) * P));
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(full, s, o);
+      kx = max(kx, __shfl_down_sync(full, kx, o));
+      kn = min(kn, __shfl_down_sync(full, kn, o));
+    }
+  }
 }
 
 enum { MODE_RHS = 0, MODE_STAGE = 1 };
@@ -245,8 +288,8 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
   const int ic = active ? i : 0, jc = active ? j : 0;
   const double tau = dt[0], tm = dt[1];
   const double inv_tm = 1.0 / tm;
-  double L[F][9];
-  cell_rhs2d<SYS, BC>(g, uin, mesh, ic, jc, inv_tm, L);
+  RhsAcc<F> R;
+  cell_rhs2d<SYS, BC>(g, uin, mesh, ic, jc, inv_tm, R);
   const long long P = g.plane;
   const long long base = (long long)mesh * F * 9 * P + (long long)jc * g.nx + ic;
   if (MODE == MODE_RHS) {
@@ -254,9 +297,17 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int m = 0; m < 9; ++m) out[base + (f * 9 + m) * P] = L[f][m];
+        for (int m = 0; m < 9; ++m)
+          out[base + (f * 9 + m) * P] = fma((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0, R.at(f, m / 3, m % 3),
+                                            -inv_tm * __ldg(uin + base + (f * 9 + m) * P));
     return;
   } else {
+    // u_out = ca u^n + cb (u_in + tau L(u_in)) with L = c_ab R - u_in / tau_max
+    //       = ca u^n + cb alpha u_in + cb tau c_ab R,   alpha = 1 - tau / tau_max:
+    // alpha = 0 unless the step is clipped at the end time, and then the cell's
+    // own coefficients drop out (the two u_in terms cancel exactly).
+    const double alpha = tau == tm ? 0.0 : (tm - tau) / tm;
+    const double cba = cb * alpha, cbt = cb * tau;
     __shared__ double sh[96];
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -264,13 +315,15 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 #pragma unroll
       for (int m = 0; m < 9; ++m) {
         const long long id = base + (f * 9 + m) * P;
-        double s = fma(tau, L[f][m], __ldg(uin + id));
-        if (ca != 0.0) s = fma(ca, __ldg(un + id), cb * s);
+        double s = (cbt * ((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0)) * R.at(f, m / 3, m % 3);
+        if (cba != 0.0) s = fma(cba, __ldg(uin + id), s);
+        if (ca != 0.0) s = fma(ca, __ldg(un + id), s);
         v[m] = s;
         if (active) out[id] = s;
       }
-      // values at the cell's own 3x3 Gauss points: x-contraction then y
-      double mx = -DINF, mn = DINF;
+      // values at the cell's own 3x3 Gauss points: x-contraction then y; their
+      // extrema as integer keys
+      long long kx = LLONG_MIN, kn = LLONG_MAX;
 #pragma unroll
       for (int qy = 0; qy < 3; ++qy) {
         double t[3];
@@ -279,22 +332,22 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
           t[a] = fma(lp(2, gnode(qy)), v[6 + a], fma(gnode(qy), v[3 + a], v[a]));
 #pragma unroll
         for (int qx = 0; qx < 3; ++qx) {
-          const double val = fma(lp(2, gnode(qx)), t[2], fma(gnode(qx), t[1], t[0]));
-          mx = fmax(mx, val);
-          mn = fmin(mn, val);
+          const long long k = dkey(fma(lp(2, gnode(qx)), t[2], fma(gnode(qx), t[1], t[0])));
+          kx = max(kx, k);
+          kn = min(kn, k);
         }
       }
       double s = active ? v[0] : 0.0;
       if (!active) {
-        mx = -DINF;
-        mn = DINF;
+        kx = LLONG_MIN;
+        kn = LLONG_MAX;
       }
-      block_reduce3(s, mx, mn, sh);
+      block_reduce_sum_keys(s, kx, kn, sh);
       if (threadIdx.x == 0) {
         double* p = pblk + f * 3;
         p[0] = s;
-        p[1] = mx;
-        p[2] = mn;
+        p[1] = dunkey(kx);
+        p[2] = dunkey(kn);
       }
     }
   }
@@ -323,12 +376,12 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
   double bx, by;
   if (SYS == SYS_EULER) {
     const double rho = __ldg(us), mx = __ldg(us + 9 * P), my = __ldg(us + 18 * P), E = __ldg(us + 27 * P);
-    const double r = 1.0 / rho;
+    const double r = rcp_pos(rho);  // NaN for rho <= 0 or subnormal: flagged below
     const double vx = mx * r, vy = my * r;
     const double p = (g.gamma - 1.0) * fma(-0.5, fma(mx, vx, my * vy), E);
     double c = 0.0;
     if (rho > 0.0 && p > 0.0) {
-      c = sqrt(g.gamma * p * r);
+      c = sqrt_pos(fma(g.gamma * p, r, SQ_FLOOR));
     } else {
       atomicOr(status, ST_NONPHYSICAL);
     }
