@@ -412,8 +412,9 @@ def run_time_to_solution(args, ws, rank, local):
     """The two 1D workloads run to their end time (1D advection, 128 cells,
     T = 2 pi; 1D Euler Shu-Osher, 4000 cells, T = 1.8): launch-bound, so the
     figure is the time to solution, with one launch per kernel
-    (cdg_step_async) and with the step replayed as a CUDA graph
-    (cdg_step_graph); the two results must be identical."""
+    (cdg_step_async), with the step replayed as a CUDA graph (cdg_step_graph)
+    and with all steps in one persistent cooperative launch
+    (cdg_step_persistent); the three results must be identical."""
     import torch
     from paper_2503_12473_gb300 import oecdg as G
     from paper_2503_12473_gb300 import workloads as W
@@ -433,9 +434,10 @@ def run_time_to_solution(args, ws, rank, local):
             t = ctx.cdg_get_time()
             nsteps += 1
         res = {}
-        for mode in ("kernels", "graph"):
+        steppers = {"kernels": ctx.cdg_step_async, "graph": ctx.cdg_step_graph,
+                    "persistent": ctx.cdg_step_persistent}
+        for mode, step in steppers.items():
             u = u0.clone()
-            step = ctx.cdg_step_async if mode == "kernels" else ctx.cdg_step_graph
             step(u, 0.0, w.T, 3)  # warm-up (and, for the graph, its capture for this u)
             u.copy_(u0)
             torch.cuda.synchronize()
@@ -449,24 +451,26 @@ def run_time_to_solution(args, ws, rank, local):
             if ctx.cdg_check_status() != G.CDG_OK:
                 raise RuntimeError("non-physical state")
             res[mode] = (ev0.elapsed_time(ev1), ctx.cdg_launch_count() - l0, u, ctx.cdg_get_time())
-    same = bool(torch.equal(res["kernels"][2], res["graph"][2]))
+    same = bool(torch.equal(res["kernels"][2], res["graph"][2]) and torch.equal(res["kernels"][2], res["persistent"][2]))
     dof = ctx.cdg_state_numel()
     line = {"metric": f"time to solution, {w.name} to T = {w.T:.6g}", "workload": w.name, "steps": nsteps,
-            "dof": dof, "t_final": res["graph"][3],
-            "kernels": {"ms": res["kernels"][0], "us_per_step": 1e3 * res["kernels"][0] / nsteps,
-                        "gpu_launches": res["kernels"][1]},
-            "graph": {"ms": res["graph"][0], "us_per_step": 1e3 * res["graph"][0] / nsteps,
-                      "gpu_launches": res["graph"][1]},
-            "speedup_graph": res["kernels"][0] / res["graph"][0], "identical": same,
-            "dof_updates_per_s_graph": 3.0 * dof * nsteps / (res["graph"][0] * 1e-3),
-            "unit_time": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic"}
+            "dof": dof, "t_final": res["persistent"][3],
+            "identical": same, "unit_time": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic"}
+    for mode in steppers:
+        line[mode] = {"ms": res[mode][0], "us_per_step": 1e3 * res[mode][0] / nsteps,
+                      "gpu_launches": res[mode][1],
+                      "dof_updates_per_s": 3.0 * dof * nsteps / (res[mode][0] * 1e-3)}
+    line["speedup_graph"] = res["kernels"][0] / res["graph"][0]
+    line["speedup_persistent"] = res["kernels"][0] / res["persistent"][0]
     print(json.dumps(line), flush=True)
 
 
 def run_batched(args, ws, rank, local):
     """256 independent periodic 2D Euler Q^2 problems (seeded sizes in
-    {64,...,512}^2 and data): one graph-captured batched launch per phase
-    against per-instance launches of the same kernels, same steps."""
+    {64,...,512}^2 and data): all steps in one persistent cooperative launch
+    (autotuned tile height and grid) against the graph-captured batched
+    launches per phase and against per-instance launches of the same kernels,
+    same steps; the three results must be identical."""
     import torch
     from paper_2503_12473_gb300 import oecdg as G
     from paper_2503_12473_gb300 import workloads as W
@@ -492,7 +496,7 @@ def run_batched(args, ws, rank, local):
     launches0 = batch.cdg_batch_launch_count()
     torch.cuda.synchronize()
     ev[0].record(stream)
-    batch.cdg_batch_step(ub, args.steps, use_graph=True)
+    batch.cdg_batch_step(ub, args.steps, persistent=True)
     ev[1].record(stream)
     torch.cuda.synchronize()
     st = batch.cdg_batch_check_status()
@@ -500,6 +504,19 @@ def run_batched(args, ws, rank, local):
         raise G.CdgError(st, "batched steps")
     launches = batch.cdg_batch_launch_count() - launches0
     ms_b = ev[0].elapsed_time(ev[1])
+    bps, pgrid = batch.cdg_batch_grid()
+    # the same steps as per-phase launches captured in a graph
+    ug = [u.clone() for u in u0]
+    batch.cdg_batch_step(ug, 1, use_graph=True)  # capture a 1-step graph once (warm-up)
+    ug = [u.clone() for u in u0]
+    torch.cuda.synchronize()
+    evg = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    evg[0].record(stream)
+    for _ in range(args.steps):
+        batch.cdg_batch_step(ug, 1, use_graph=True)
+    evg[1].record(stream)
+    torch.cuda.synchronize()
+    ms_g = evg[0].elapsed_time(evg[1])
     # per-instance launches of the same kernels on the same stream
     ui = [u.clone() for u in u0]
     for c, u in zip(ctxs, ui):
@@ -514,13 +531,21 @@ def run_batched(args, ws, rank, local):
     torch.cuda.synchronize()
     ms_i = ev[2].elapsed_time(ev[3])
     diff = max(((a - b).abs().sum() / b.abs().sum()).item() for a, b in zip(ub, ui))
+    same = all(torch.equal(a, b) for a, b in zip(ub, ug))  # persistent vs per-phase, same tile height
+    # the single-mesh kernels use 4-row tiles: bitwise equal to the batch when it does too
+    same_pi = all(torch.equal(a, b) for a, b in zip(ub, ui)) if rows == 4 else None
     line = {"metric": "FP64 DOF-updates/s per RK stage, batched 2D Euler Q2 (256 meshes)", "impl": "ours",
             "workload": f"batched_{args.count}_seed{args.seed}", "value": 3.0 * dof * args.steps / (ms_b * 1e-3),
             "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
             "dof": dof, "sizes": sorted({q.n for q in insts}), "rows": rows, "gpu_launches": launches,
+            "persistent_grid": {"blocks_per_sm": bps, "blocks": pgrid},
+            "graph_per_phase": {"value": 3.0 * dof * args.steps / (ms_g * 1e-3), "ms_per_step": ms_g / args.steps,
+                                "launches_per_step": 11},
             "per_instance": {"value": 3.0 * dof * args.steps / (ms_i * 1e-3), "ms_per_step": ms_i / args.steps,
                              "launches_per_step": 12 * args.count},
-            "speedup_vs_per_instance": ms_i / ms_b, "max_rel_l1_batched_vs_per_instance": diff,
+            "speedup_vs_per_instance": ms_i / ms_b, "speedup_vs_graph_per_phase": ms_g / ms_b,
+            "identical_persistent_vs_per_phase": same, "identical_vs_per_instance": same_pi,
+            "max_rel_l1_batched_vs_per_instance": diff,
             "dtype": "f64", "data": "synthetic"}
     print(json.dumps(line), flush=True)
 

@@ -186,6 +186,28 @@ cdg_status cdg_step_async(cdg_ctx* ctx, double* d_u, double t, double T_end, int
  * status with cdg_check_status. */
 cdg_status cdg_step_graph(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
 
+/* As cdg_step_async, for 1D meshes (whose steps are far too small to fill the
+ * GPU, so that a step is bound by the latency of its launches): all nsteps
+ * steps of Eq. (eq:RKCDG) -- the wave speed and tau, and every stage's CDG
+ * right-hand side, RK combination, sigma and OE step -- run in ONE cooperative
+ * launch whose blocks meet at grid-wide barriers between those phases.  Same
+ * per-cell code and fixed-order reductions as cdg_step: the results are equal
+ * bit for bit.  Every barrier wait is bounded (cdg_set_wait; 5 s by default);
+ * a wait that runs out makes every block leave the kernel and sets the status
+ * that cdg_check_status reports as CDG_ETIMEOUT (d_u is then partly advanced).
+ * The first call allocates a small scratch (one double per block of the grid
+ * and the barrier counter) in the context.  Asynchronous; not for use inside a
+ * stream capture (the first call allocates).  Errors: CDG_EINVAL,
+ * CDG_EUNSUPPORTED (2D contexts), CDG_ENOMEM, CDG_ECUDA. */
+cdg_status cdg_step_persistent(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps);
+
+/* Bounded wait of the grid barriers of cdg_step_persistent: a block that has
+ * waited limit_s seconds (0 < limit_s <= 3600) at one barrier gives up (status
+ * CDG_ETIMEOUT).  withheld >= 0 is a test hook: every barrier then waits for
+ * that many more arrivals than there are blocks, which never come, so that a
+ * test can make the wait run out on purpose (0 for normal use). */
+cdg_status cdg_set_wait(cdg_ctx* ctx, double limit_s, int withheld);
+
 /* Device time after the last cdg_step / cdg_step_async; synchronises. */
 cdg_status cdg_get_time(cdg_ctx* ctx, double* t);
 
@@ -225,7 +247,8 @@ cdg_status cdg_step_record(cdg_ctx* ctx, double* d_u, double* d_rec);
 cdg_status cdg_step_adjoint_recorded(cdg_ctx* ctx, const double* d_rec, const double* d_lam_next, double* d_lam,
                                      double* d_gtau);
 
-/* Read and clear the device status flag (synchronises): CDG_OK or
+/* Read and clear the device status flag (synchronises): CDG_OK,
+ * CDG_ETIMEOUT (a grid barrier of cdg_step_persistent ran out of time) or
  * CDG_ENONPHYSICAL. */
 cdg_status cdg_check_status(cdg_ctx* ctx);
 
@@ -299,9 +322,16 @@ cdg_status cdg_math_eval(int op, const double* d_x, size_t n, double* d_y, void*
  * Many independent 2D Euler Q^2 problems of uneven mesh sizes advanced together.
  * Not in the paper: each instance is exactly the single-mesh scheme above
  * (Eq. (eq:RKCDG) with SSP-RK3 and the OE step), with its own sigma, wave speed,
- * tau and time.  Every phase of a step is one launch over the tiles of all
- * instances (11 launches per step whatever the number of instances), and the
- * launches of nsteps steps can be captured in a CUDA graph. */
+ * tau and time.  Two ways to run the steps, with bitwise-equal results:
+ *   - per-phase launches: every phase of a step is one launch over the tiles
+ *     of all instances (11 launches per step whatever the number of
+ *     instances), optionally captured in a CUDA graph;
+ *   - persistent: ONE cooperative launch runs all nsteps steps; its blocks
+ *     loop over the same tiles phase by phase and meet at grid-wide barriers.
+ *     Every barrier wait is bounded (cdg_batch_set_wait; 5 s by default): a
+ *     wait that runs out sets the batch's status to CDG_ETIMEOUT and every
+ *     block leaves the kernel, so nothing hangs.  The launch can also be
+ *     captured in a CUDA graph. */
 typedef struct cdg_batch cdg_batch;
 
 /* Create a batch of n instances (descs[q]: dim 2, k 2, basis Q, system Euler,
@@ -321,12 +351,40 @@ const char* cdg_batch_last_error(const cdg_batch* batch);
 /* nsteps SSP-RK3 steps of every instance, in place on the caller's device
  * states d_us[0..n-1] (a host array of n device pointers, each with the
  * single-mesh layout of its instance).  The instance table is re-uploaded
- * (synchronously) only when the pointers change.  use_graph != 0: the launches
- * of nsteps steps are captured once in a CUDA graph (re-captured when nsteps or
- * the pointers change) and the graph is launched.  Asynchronous otherwise. */
-cdg_status cdg_batch_step(cdg_batch* batch, double* const* d_us, int nsteps, int use_graph);
+ * (synchronously) only when the pointers change.  flags:
+ *   0                                         per-phase launches;
+ *   CDG_BATCH_GRAPH                           per-phase launches of nsteps steps
+ *                                             captured once in a CUDA graph;
+ *   CDG_BATCH_PERSISTENT                      one persistent cooperative launch
+ *                                             for all nsteps steps;
+ *   CDG_BATCH_PERSISTENT | CDG_BATCH_GRAPH    that launch captured in a graph.
+ * A graph is re-captured when nsteps, flags, the pointers or the batch's
+ * settings change.  Asynchronous; check the outcome (CDG_ENONPHYSICAL,
+ * CDG_ETIMEOUT) with cdg_batch_check_status.  Errors: CDG_EINVAL (bad
+ * pointers, nsteps < 0, flags outside 0..3), CDG_ECUDA (a launch failed, for
+ * example a persistent grid that does not fit the device). */
+enum { CDG_BATCH_GRAPH = 1, CDG_BATCH_PERSISTENT = 2 };
+cdg_status cdg_batch_step(cdg_batch* batch, double* const* d_us, int nsteps, int flags);
 
-/* Read and clear the batch's status flag (synchronises): CDG_OK or
+/* Bounded wait of the persistent kernel's grid barriers: a block that has
+ * waited limit_s seconds (0 < limit_s <= 3600) at one barrier gives up and the
+ * batch's status becomes CDG_ETIMEOUT.  withheld >= 0 is a test hook: every
+ * barrier then waits for that many more arrivals than there are blocks, which
+ * never come, so that a test can make the wait run out on purpose (0 for
+ * normal use).  Synchronises the batch's stream. */
+cdg_status cdg_batch_set_wait(cdg_batch* batch, double limit_s, int withheld);
+
+/* Persistent grid: blocks_per_sm blocks on every SM (0 = as many as fit the
+ * register and shared-memory budget of the kernel for the current tile
+ * height; more than fit is clamped).  Synchronises the batch's stream. */
+cdg_status cdg_batch_set_grid(cdg_batch* batch, int blocks_per_sm);
+
+/* The persistent grid in use: blocks per SM and the total block count. */
+cdg_status cdg_batch_grid(const cdg_batch* batch, int* blocks_per_sm, int* grid);
+
+/* Read and clear the batch's status flag (synchronises): CDG_OK,
+ * CDG_ETIMEOUT (a persistent grid barrier ran out of time; the instances' states
+ * are then partly advanced and must be restored by the caller) or
  * CDG_ENONPHYSICAL. */
 cdg_status cdg_batch_check_status(cdg_batch* batch);
 
@@ -342,11 +400,15 @@ cdg_status cdg_batch_set_rows(cdg_batch* batch, int rows);
 /* Tile height (rows of 32 cells per block: 2, 4 or 8) currently in use. */
 cdg_status cdg_batch_rows(const cdg_batch* batch, int* rows);
 
-/* Pick the tile height for this batch: look it up in the JSON cache file
- * `cache_path` (keyed by a signature of the mesh sizes; NULL: no cache), or
- * time one stage + sigma + OE pass of each candidate (2, 4, 8 rows; it reads
- * the states d_us and writes only scratch) and store the fastest.  Resets the
- * instances' time to 0.  *rows_out (nullable) receives the choice. */
+/* Pick the tile height (2, 4 or 8 rows of 32 cells per block) and the
+ * persistent grid (blocks per SM, 1 up to what fits for that height) for this
+ * batch: look them up in the JSON cache file `cache_path` (keyed by a
+ * signature of the mesh sizes; NULL: no cache; value rows * 100 + blocks per
+ * SM), or time the persistent kernel on one first stage of every instance for
+ * each candidate (it reads the states d_us and writes only scratch) and store
+ * the fastest.  Resets the instances' time to 0.  *rows_out (nullable)
+ * receives the tile height; cdg_batch_grid reports the grid.  Errors as
+ * cdg_batch_step, and CDG_ETIMEOUT if a timed run's barrier ran out. */
 cdg_status cdg_batch_autotune(cdg_batch* batch, double* const* d_us, const char* cache_path, int* rows_out);
 
 #ifdef __cplusplus

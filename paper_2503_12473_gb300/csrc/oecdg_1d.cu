@@ -9,6 +9,7 @@
 
 #include "oecdg_common.cuh"
 #include "oecdg_kernels.h"
+#include "oecdg_persist.cuh"
 #include "oecdg_poly.cuh"
 
 namespace oecdg {
@@ -33,7 +34,9 @@ __device__ __forceinline__ void flux1(const Geo& g, const double* w, double* f) 
   if (SYS == SYS_EULER) {
     const double r = __drcp_rn(w[0]);
     const double v = w[1] * r;
-    const double p = (g.gamma - 1.0) * (w[2] - 0.5 * w[1] * v);
+    // multiply-adds written out as fma: every kernel that inlines this rounds
+    // alike (the compiler's own contraction may differ between them)
+    const double p = (g.gamma - 1.0) * fma(-0.5 * w[1], v, w[2]);
     f[0] = w[1];
     f[1] = fma(w[1], v, p);
     f[2] = (w[2] + p) * v;
@@ -49,7 +52,7 @@ template <int SYS>
 __device__ __forceinline__ double speed1(const Geo& g, const double* w) {
   if (SYS == SYS_EULER) {
     const double v = w[1] / w[0];
-    const double p = (g.gamma - 1.0) * (w[2] - 0.5 * w[1] * v);
+    const double p = (g.gamma - 1.0) * fma(-0.5 * w[1], v, w[2]);
     if (!(w[0] > 0.0 && p > 0.0)) return -1.0;
     return fabs(v) + sqrt(g.gamma * p / w[0]);
   } else if (SYS == SYS_BURGERS) {
@@ -60,7 +63,7 @@ __device__ __forceinline__ double speed1(const Geo& g, const double* w) {
 
 // L_a = (2a+1) [ sum_{s,q} (w_q/4)(w/tau_max) P_a(xi) + (1/h) sum (w_q/2) f(w) P_a'(xi)
 //               - (1/h)(f_R - (-1)^a f_L) ] - u_a / tau_max
-template <int SYS, int BC, int K>
+template <int SYS, int BC, int K, int LD = LD_NC>
 __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restrict__ u, int mesh, int i, double inv_tm,
                                            double (&L)[Fields1<SYS>::F][K + 1]) {
   constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
@@ -81,7 +84,7 @@ __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restric
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int a = 0; a < M; ++a) w[f][a] = __ldg(c + (f * M + a) * P);
+      for (int a = 0; a < M; ++a) w[f][a] = ldv<LD>(c + (f * M + a) * P);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       const double xo = xo1(N, sx, q), xsf = xs1(N, sx, q);
@@ -121,8 +124,8 @@ __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restric
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const double face = fR[f] - ((a & 1) ? -fL[f] : fL[f]);
-      const double br = 0.25 * inv_tm * Ad[f][a] + ih * (0.5 * Bd[f][a] - face);
-      L[f][a] = fma((double)(2 * a + 1), br, -inv_tm * __ldg(us + (f * M + a) * P));
+      const double br = fma(0.25 * inv_tm, Ad[f][a], ih * fma(0.5, Bd[f][a], -face));
+      L[f][a] = fma((double)(2 * a + 1), br, -inv_tm * ldv<LD>(us + (f * M + a) * P));
     }
 }
 
@@ -132,19 +135,17 @@ enum { MODE1_RHS = 0, MODE1_STAGE = 1 };
 // MODE1_STAGE: out = sum_m cb.c[m] cb.u[m] + cb.ct tau L(uin)  (one Shu-Osher
 //              stage), plus per-block sigma partials of out: sum of the cell
 //              averages and max / min over the cell's K+1 Gauss points.
-template <int SYS, int BC, int K, int MODE>
-__global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict__ uin, StageComb cb,
-                                                 double* __restrict__ out, const double* __restrict__ dt,
-                                                 double* __restrict__ partials) {
+template <int SYS, int BC, int K, int MODE, int LD = LD_NC>
+__device__ __forceinline__ void stage_cell1d(const Geo& g, const double* __restrict__ uin, const StageComb& cb,
+                                             double* __restrict__ out, const double* __restrict__ dt,
+                                             double* __restrict__ pblk, int mesh, int i) {
   constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
-  const int mesh = blockIdx.y;
-  const int i = blockIdx.x * NT1 + threadIdx.x;
   const bool active = i < g.nx;
   const int ic = active ? i : 0;
-  const double tau = dt[0], tm = dt[1];
+  const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
   const double inv_tm = 1.0 / tm;
   double L[F][M];
-  cell_rhs1d<SYS, BC, K>(g, uin, mesh, ic, inv_tm, L);
+  cell_rhs1d<SYS, BC, K, LD>(g, uin, mesh, ic, inv_tm, L);
   const long long P = g.plane;
   const long long base = (long long)mesh * F * M * P + ic;
   if (MODE == MODE1_RHS) {
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
         double s = tl * L[f][a];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
-          if (m < cb.n) s = fma(cb.c[m], __ldg(cb.u[m] + id), s);
+          if (m < cb.n) s = fma(cb.c[m], ldv<LD>(cb.u[m] + id), s);
         v[a] = s;
         if (active) out[id] = s;
       }
@@ -186,8 +187,7 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
       }
       block_reduce3(s, mx, mn, sh);
       if (threadIdx.x == 0) {
-        const long long nblk = gridDim.x;
-        double* p = partials + ((mesh * nblk + blockIdx.x) * F + f) * 3;
+        double* p = pblk + f * 3;
         p[0] = s;
         p[1] = mx;
         p[2] = mn;
@@ -196,17 +196,25 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
   }
 }
 
+template <int SYS, int BC, int K, int MODE>
+__global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict__ uin, StageComb cb,
+                                                 double* __restrict__ out, const double* __restrict__ dt,
+                                                 double* __restrict__ partials) {
+  constexpr int F = Fields1<SYS>::F;
+  const int mesh = blockIdx.y;
+  stage_cell1d<SYS, BC, K, MODE>(g, uin, cb, out, dt, partials + (mesh * (long long)gridDim.x + blockIdx.x) * F * 3,
+                                 mesh, blockIdx.x * NT1 + threadIdx.x);
+}
+
 // delta^m = (2m+1) h^{m-1} / ((2K-1) m!) beta (|d^m (u^C-u^D)|_R + |...|_L) / sigma
 // for m = 0..K, max over fields; then the exact damping of mode a by
 // exp(-tau sum_{m <= a} delta^m).  The face points are the cell ends xi = +-1,
 // which are the centres (xi' = 0) of the two overlapping cells.
-template <int SYS, int BC, int K, bool WRITE_DELTA>
-__global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
-                                              const double* __restrict__ dt, const double* __restrict__ sigma,
-                                              double* __restrict__ delta_out, int* __restrict__ status) {
+template <int SYS, int BC, int K, bool WRITE_DELTA, int LD = LD_NC>
+__device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
+                                          const double* __restrict__ dt, const double* __restrict__ sigma,
+                                          double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i) {
   constexpr int F = Fields1<SYS>::F, M = K + 1;
-  const int mesh = blockIdx.y;
-  const int i = blockIdx.x * NT1 + threadIdx.x;
   if (i >= g.nx) return;
   const long long P = g.plane;
   const double* us = uh + (long long)mesh * F * M * P + i;
@@ -215,7 +223,7 @@ __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ 
   const int oL = wrap_index<BC>(i + off, g.nx), oR = wrap_index<BC>(i + 1 + off, g.nx);
   double wa[F];
 #pragma unroll
-  for (int f = 0; f < F; ++f) wa[f] = __ldg(us + (f * M) * P);
+  for (int f = 0; f < F; ++f) wa[f] = ldv<LD>(us + (f * M) * P);
   double beta = speed1<SYS>(g, wa);
   if (beta < 0.0) {
     atomicOr(status, ST_NONPHYSICAL);
@@ -237,13 +245,13 @@ __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ 
   for (int m = 0; m < M; ++m) dl[m] = 0.0;
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    const double sg = __ldg(sigma + mesh * F + f);
+    const double sg = ldv<LD>(sigma + mesh * F + f);
     double u[M], l[M], r[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      u[a] = __ldg(us + (f * M + a) * P);
-      l[a] = __ldg(uo + (f * M + a) * P + oL);
-      r[a] = __ldg(uo + (f * M + a) * P + oR);
+      u[a] = ldv<LD>(us + (f * M + a) * P);
+      l[a] = ldv<LD>(uo + (f * M + a) * P + oL);
+      r[a] = ldv<LD>(uo + (f * M + a) * P + oR);
     }
     if (sg != 0.0) {
       const double is = beta / sg;
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ 
     for (int m = 0; m < M; ++m) dp[m] = dl[m];
   }
   if (usig != nullptr) {
-    const double tau = dt[0];
+    const double tau = ldv<LD>(dt);
     double e[M];
     double rate = dl[0];
 #pragma unroll
@@ -280,11 +288,19 @@ __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ 
     double* os = usig + (long long)mesh * F * M * P + i;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-      os[(f * M) * P] = __ldg(us + (f * M) * P);
+      os[(f * M) * P] = ldv<LD>(us + (f * M) * P);
 #pragma unroll
-      for (int a = 1; a < M; ++a) os[(f * M + a) * P] = __ldg(us + (f * M + a) * P) * e[a];
+      for (int a = 1; a < M; ++a) os[(f * M + a) * P] = ldv<LD>(us + (f * M + a) * P) * e[a];
     }
   }
+}
+
+template <int SYS, int BC, int K, bool WRITE_DELTA>
+__global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
+                                              const double* __restrict__ dt, const double* __restrict__ sigma,
+                                              double* __restrict__ delta_out, int* __restrict__ status) {
+  oe_cell1d<SYS, BC, K, WRITE_DELTA>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.y,
+                                     blockIdx.x * NT1 + threadIdx.x);
 }
 
 template <int SYS, int K>
@@ -360,6 +376,88 @@ __global__ void k_project1d(Geo g, const double* __restrict__ vals, double* __re
   }
 }
 
+// ------------------------------------------------------- persistent step --
+
+// Maximum wave speed over the cell averages of both meshes of `u`, grid-stride
+// (the same speeds as k_wave1d), into wpart[blockIdx.x]; the last block to
+// finish takes the maximum over all blocks and sets (tau, tau_max, time)
+// exactly as k_dt_final does.
+template <int SYS, int K>
+__device__ __forceinline__ void persist_wave1d(const Geo& g, const Persist1& a, const double* u, double* sh) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
+  const long long ncell = 2 * g.plane;
+  double mx = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int mesh = (int)(c / g.plane);
+    const double* uc = u + (long long)mesh * F * M * g.plane + (c - mesh * g.plane);
+    double w[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) w[f] = ldv<LD_CA>(uc + (f * M) * g.plane);
+    const double sp = speed1<SYS>(g, w);
+    if (sp >= 0.0) mx = fmax(mx, sp);
+    else atomicOr(a.status, ST_NONPHYSICAL);
+  }
+  mx = block_reduce_max(mx, sh);
+  if (threadIdx.x == 0) a.wpart[blockIdx.x] = mx;
+  if (last_block(a.bar + 1)) {
+    // all threads of the last block fold the partials (the maximum is exact:
+    // any order gives k_dt_final's value)
+    double bx = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) bx = fmax(bx, ldv<LD_CA>(a.wpart + b));
+    __syncthreads();  // sh is reused
+    bx = block_reduce_max(bx, sh);
+    if (threadIdx.x == 0) finish_dt(bx, 0.0, g.hx, g.hy, 1, g.cfl, a.T_end, a.dt, a.time);
+  }
+}
+
+// nsteps steps in one cooperative launch.  Phases, each ended by a grid
+// barrier with a bounded wait: [stage tiles, then sigma by the last block to
+// finish them] -> [OE tiles (or a copy without OE); after the last stage of a
+// step, the next step's wave speeds and tau, by the last block] per stage, plus
+// one wave-speed phase before the first step: 2 barriers per stage.  Stage
+// tile b is mesh b & 1, stage block b >> 1 of the per-phase layout, so the
+// sigma partials land where the per-phase kernel puts them; the wave speeds
+// come from u_h's cell averages, which the OE step leaves unchanged.
+template <int SYS, int BC, int K>
+__global__ void __launch_bounds__(NT1) k_persist1d(Geo g, Persist1 a) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
+  __shared__ double sh[32];
+  const long long ntiles = 2 * a.nblk;
+  persist_wave1d<SYS, K>(g, a, a.uin[0], sh);
+  if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+  for (int s = 0; s < a.nsteps; ++s) {
+    for (int l = 0; l < a.nst; ++l) {
+      for (long long b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int mesh = (int)(b & 1);
+        const long long blk = b >> 1;
+        stage_cell1d<SYS, BC, K, MODE1_STAGE, LD_CA>(g, a.uin[l], a.cb[l], a.ua, a.dt,
+                                                     a.partials + (mesh * a.nblk + blk) * F * 3, mesh,
+                                                     (int)(blk * NT1) + threadIdx.x);
+      }
+      if (a.oe && last_block(a.bar + 1)) {
+        for (int it = threadIdx.x >> 5; it < 2 * F; it += blockDim.x >> 5)
+          warp_sigma<LD_CA>(a.partials, a.nblk, F, it / F, it % F, g.plane, a.avg, a.sigma);
+      }
+      if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+      if (a.oe) {
+        for (long long b = blockIdx.x; b < ntiles; b += gridDim.x)
+          oe_cell1d<SYS, BC, K, false, LD_CA>(g, a.ua, a.dst[l], a.dt, a.sigma, nullptr, a.status, (int)(b & 1),
+                                              (int)((b >> 1) * NT1) + threadIdx.x);
+      } else {
+        const long long n = 2LL * F * M * g.plane;
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+             q += (long long)gridDim.x * blockDim.x)
+          a.dst[l][q] = ldv<LD_CA>(a.ua + q);
+      }
+      const bool last = l == a.nst - 1 && s + 1 == a.nsteps;
+      if (last) return;  // the kernel's end orders everything for the host
+      if (l == a.nst - 1) persist_wave1d<SYS, K>(g, a, a.ua, sh);
+      if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+    }
+  }
+}
+
 // ----------------------------------------------------------------- launch --
 
 template <int V>
@@ -419,6 +517,49 @@ cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* p
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_dt_final(partial, nblk, g.hx, g.hy, 1, g.cfl, T_end, dt, time, st);
+}
+
+// One block per SM: a 1D step is latency-bound and the FP64 pipe of an SM is
+// shared by its blocks, so the persistent grid spreads its blocks over the
+// SMs (each block reserves more than half of an SM's shared memory, which the
+// kernel does not use, so that no two blocks share an SM) and loops over the
+// tiles when there are more tiles than SMs.
+constexpr size_t PERSIST1_SMEM = 120 * 1024;
+
+cudaError_t persist_grid_1d(int sys, int bc, int k, const Geo& g, int nsm, long long* grid) {
+  cudaError_t e = cudaSuccess;
+  int occ = 0;
+  by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
+    auto kern = k_persist1d<decltype(S)::value, decltype(B)::value, decltype(Kc)::value>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PERSIST1_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT1, PERSIST1_SMEM);
+  });
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  long long gsz = (long long)occ * nsm;
+  const long long tiles = 2 * partial_blocks_1d(g);
+  *grid = gsz < tiles ? gsz : tiles;
+  return cudaSuccess;
+}
+
+cudaError_t launch_persist1d(int sys, int bc, int k, const Geo& g, const Persist1& a, long long grid,
+                             cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned long long), st);  // barrier, tickets
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT1);
+  cfg.dynamicSmemBytes = PERSIST1_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
+    e = cudaLaunchKernelEx(&cfg, k_persist1d<decltype(S)::value, decltype(B)::value, decltype(Kc)::value>, g, a);
+  });
+  return e;
 }
 
 cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st) {

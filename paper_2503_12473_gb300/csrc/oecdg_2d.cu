@@ -2,6 +2,7 @@
 // launch wrappers around the per-cell code of oecdg_2d_body.cuh.
 #include "oecdg_2d_body.cuh"
 #include "oecdg_kernels.h"
+#include "oecdg_persist.cuh"
 
 namespace oecdg {
 
@@ -36,25 +37,11 @@ __global__ void __launch_bounds__(NT, OECDG_STAGE_MINB) k_stage2d(Geo g, const d
 
 // Fixed-order reduction of the block partials: avg and sigma per mesh and
 // field (Section 2.2): avg = mean of the cell averages over the stored cells,
-// sigma = max(max - avg, avg - min) over the cell Gauss points.
-// grid = (F, 2), block = 1024.
+// sigma = max(max - avg, avg - min) over the cell Gauss points.  grid = (F, 2),
+// one warp each: the same code as the persistent kernels' sigma phase.
 __global__ void k_sigma(const double* __restrict__ partials, long long nblk, int F, long long ncell,
                         double* __restrict__ sigma, double* __restrict__ avg) {
-  const int f = blockIdx.x, mesh = blockIdx.y;
-  __shared__ double sh[96];
-  double s = 0.0, mx = -DINF, mn = DINF;
-  for (long long b = threadIdx.x; b < nblk; b += blockDim.x) {
-    const double* p = partials + ((mesh * nblk + b) * F + f) * 3;
-    s += p[0];
-    mx = fmax(mx, p[1]);
-    mn = fmin(mn, p[2]);
-  }
-  block_reduce3(s, mx, mn, sh);
-  if (threadIdx.x == 0) {
-    const double a = s / (double)ncell;
-    avg[mesh * F + f] = a;
-    sigma[mesh * F + f] = fmax(mx - a, a - mn);
-  }
+  warp_sigma<LD_NC>(partials, nblk, F, blockIdx.y, blockIdx.x, ncell, avg, sigma);
 }
 
 // ---------------------------------------------------------------- OE step --
@@ -94,7 +81,7 @@ __global__ void k_wave2d(Geo g, const double* __restrict__ u, double* __restrict
     if (SYS == SYS_EULER) {
       const double rho = us[0], m1 = us[9 * g.plane], m2 = us[18 * g.plane], E = us[27 * g.plane];
       const double vx = m1 / rho, vy = m2 / rho;
-      const double p = (g.gamma - 1.0) * (E - 0.5 * (m1 * vx + m2 * vy));
+      const double p = (g.gamma - 1.0) * fma(-0.5, fma(m1, vx, m2 * vy), E);
       if (rho > 0.0 && p > 0.0) {
         const double cs = sqrt(g.gamma * p / rho);
         mx = fmax(mx, fabs(vx) + cs);
@@ -116,9 +103,8 @@ __global__ void k_wave2d(Geo g, const double* __restrict__ u, double* __restrict
   }
 }
 
-// One thread: tau_max = C_CFL / (beta_x/h_x + beta_y/h_y) (1D: C_CFL h / beta),
-// tau = tau_max clipped at T_end (a step that would leave a sliver shorter
-// than 1e-12 T_end is stretched to T_end); time[0] is advanced by tau.
+// One thread: the maxima of the block partials, then finish_dt (tau_max, the
+// clipped tau, the time).
 __global__ void k_dt_final(const double* __restrict__ partial, int nblk, double hx, double hy, int dim, double cfl,
                            double T_end, double* __restrict__ dt, double* __restrict__ time) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -127,17 +113,7 @@ __global__ void k_dt_final(const double* __restrict__ partial, int nblk, double 
     bx = fmax(bx, partial[2 * b]);
     by = fmax(by, partial[2 * b + 1]);
   }
-  const double rate = bx / hx + (dim == 2 ? by / hy : 0.0);
-  const double tm = rate > 0.0 ? cfl / rate : 0.0;
-  const double t = time[0];
-  double tau = tm;
-  if (T_end > 0.0) {
-    if (t >= T_end) tau = 0.0;
-    else if (T_end - (t + tm) < 1e-12 * T_end) tau = T_end - t;
-  }
-  dt[0] = tau;
-  dt[1] = tm > 0.0 ? tm : 1.0;
-  time[0] = (T_end > 0.0 && tau == T_end - t) ? T_end : t + tau;
+  finish_dt(bx, by, hx, hy, dim, cfl, T_end, dt, time);
 }
 
 __global__ void k_set2(double* __restrict__ p, double a, double b) {
@@ -231,7 +207,7 @@ cudaError_t launch_stage2d(int sys, int bc, const Geo& g, int rhs_only, const do
 
 cudaError_t launch_sigma(const double* partials, long long nblk, int F, long long ncell, double* sigma, double* avg,
                          cudaStream_t st) {
-  k_sigma<<<dim3(F, 2), 1024, 0, st>>>(partials, nblk, F, ncell, sigma, avg);
+  k_sigma<<<dim3(F, 2), 32, 0, st>>>(partials, nblk, F, ncell, sigma, avg);
   return cudaGetLastError();
 }
 

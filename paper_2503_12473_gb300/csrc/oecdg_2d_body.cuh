@@ -13,6 +13,7 @@
 #include <climits>
 
 #include "oecdg_common.cuh"
+#include "oecdg_persist.cuh"
 
 namespace oecdg {
 
@@ -71,7 +72,7 @@ struct RhsAcc {
   __device__ __forceinline__ double& at(int f, int b, int a) { return r[f][b][a]; }
 };
 
-template <int SYS, int BC, class Acc>
+template <int SYS, int BC, int LD, class Acc>
 __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restrict__ u, int mesh, int i, int j,
                                            double inv_tm, Acc& R) {
   constexpr int F = Fields<SYS>::F;
@@ -119,7 +120,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
         for (int f = 0; f < F; ++f)
 #pragma unroll
           for (int b = 0; b < 3; ++b)
-            T[f][b] = fma(-0.5, __ldg(c + (f * 9 + b * 3 + 2) * P), __ldg(c + (f * 9 + b * 3) * P));
+            T[f][b] = fma(-0.5, ldv<LD>(c + (f * 9 + b * 3 + 2) * P), ldv<LD>(c + (f * 9 + b * 3) * P));
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const double eo = xs_other(sy, q), es = xs_self(sy, q);
@@ -135,22 +136,16 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
           }
         }
       }
-      // R += (-s) P_a(s) (4/hx) Bf, s = 2 sx - 1
-      const double sc = 4.0 / g.hx;
+      // R += (-s) P_a(s) (4/hx) Bf, s = 2 sx - 1 (explicit fma: one rounding
+      // per update, the same in every kernel that inlines this)
+      const double sc = 4.0 / g.hx, sp = sx ? -sc : sc;
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          const double v = sc * Bf[f][b];
-          if (sx) {
-            R.at(f, b, 0) -= v;
-            R.at(f, b, 1) -= v;
-            R.at(f, b, 2) -= v;
-          } else {
-            R.at(f, b, 0) += v;
-            R.at(f, b, 1) -= v;
-            R.at(f, b, 2) += v;
-          }
+          R.at(f, b, 0) = fma(sp, Bf[f][b], R.at(f, b, 0));
+          R.at(f, b, 1) = fma(-sc, Bf[f][b], R.at(f, b, 1));
+          R.at(f, b, 2) = fma(sp, Bf[f][b], R.at(f, b, 2));
         }
     }
     // ---- the three volume columns of this half
@@ -171,7 +166,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
             const double* cb = c + (f * 9 + b * 3) * P;
-            T[f][b] = fma(lp(2, xo), __ldg(cb + 2 * P), fma(xo, __ldg(cb + P), __ldg(cb)));
+            T[f][b] = fma(lp(2, xo), ldv<LD>(cb + 2 * P), fma(xo, ldv<LD>(cb + P), ldv<LD>(cb)));
           }
 #pragma unroll
         for (int qy = 0; qy < 3; ++qy) {
@@ -278,7 +273,7 @@ enum { MODE_RHS = 0, MODE_STAGE = 1 };
 // The work of one thread of a stage block: cell (i, j) of `mesh` (inactive
 // threads of a ragged tile compute a clamped cell, store nothing and give
 // neutral partials).  `pblk` = this block's partials [F][3].
-template <int SYS, int BC, int MODE>
+template <int SYS, int BC, int MODE, int LD = LD_NC>
 __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restrict__ uin,
                                              const double* __restrict__ un, double* __restrict__ out,
                                              const double* __restrict__ dt, double ca, double cb,
@@ -286,10 +281,10 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
   constexpr int F = Fields<SYS>::F;
   const bool active = i < g.nx && j < g.ny;
   const int ic = active ? i : 0, jc = active ? j : 0;
-  const double tau = dt[0], tm = dt[1];
+  const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
   const double inv_tm = 1.0 / tm;
   RhsAcc<F> R;
-  cell_rhs2d<SYS, BC>(g, uin, mesh, ic, jc, inv_tm, R);
+  cell_rhs2d<SYS, BC, LD>(g, uin, mesh, ic, jc, inv_tm, R);
   const long long P = g.plane;
   const long long base = (long long)mesh * F * 9 * P + (long long)jc * g.nx + ic;
   if (MODE == MODE_RHS) {
@@ -299,7 +294,7 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 #pragma unroll
         for (int m = 0; m < 9; ++m)
           out[base + (f * 9 + m) * P] = fma((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0, R.at(f, m / 3, m % 3),
-                                            -inv_tm * __ldg(uin + base + (f * 9 + m) * P));
+                                            -inv_tm * ldv<LD>(uin + base + (f * 9 + m) * P));
     return;
   } else {
     // u_out = ca u^n + cb (u_in + tau L(u_in)) with L = c_ab R - u_in / tau_max
@@ -316,8 +311,8 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
       for (int m = 0; m < 9; ++m) {
         const long long id = base + (f * 9 + m) * P;
         double s = (cbt * ((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0)) * R.at(f, m / 3, m % 3);
-        if (cba != 0.0) s = fma(cba, __ldg(uin + id), s);
-        if (ca != 0.0) s = fma(ca, __ldg(un + id), s);
+        if (cba != 0.0) s = fma(cba, ldv<LD>(uin + id), s);
+        if (ca != 0.0) s = fma(ca, ldv<LD>(un + id), s);
         v[m] = s;
         if (active) out[id] = s;
       }
@@ -358,7 +353,7 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 // ISO = true requires hx == hy: every m-th derivative then carries the same
 // factor (2/h)^m, so the traces stay in reference units and the factor is
 // applied once, in the constants of delta^m (the recorded sums are physical).
-template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false>
+template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false, int LD = LD_NC>
 __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
@@ -375,7 +370,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
   // wave speeds beta_{e,K} at the cell average
   double bx, by;
   if (SYS == SYS_EULER) {
-    const double rho = __ldg(us), mx = __ldg(us + 9 * P), my = __ldg(us + 18 * P), E = __ldg(us + 27 * P);
+    const double rho = ldv<LD>(us), mx = ldv<LD>(us + 9 * P), my = ldv<LD>(us + 18 * P), E = ldv<LD>(us + 27 * P);
     const double r = rcp_pos(rho);  // NaN for rho <= 0 or subnormal: flagged below
     const double vx = mx * r, vy = my * r;
     const double p = (g.gamma - 1.0) * fma(-0.5, fma(mx, vx, my * vy), E);
@@ -405,11 +400,11 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
   double rs[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    const double sg = __ldg(sigma + mesh * F + f);
+    const double sg = ldv<LD>(sigma + mesh * F + f);
     const double* cs = us + f * 9 * P;
     double u[9];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) u[m] = __ldg(cs + m * P);
+    for (int m = 0; m < 9; ++m) u[m] = ldv<LD>(cs + m * P);
     double Sx0 = 0.0, Sx1 = 0.0, Sx2 = 0.0, Sy0 = 0.0, Sy1 = 0.0, Sy2 = 0.0;
     // Faces normal to direction n (0: x, 1: y), at reference coordinate s of K.
     // Along the face, K's trace and its normal derivatives of order 0, 1, 2 are
@@ -445,9 +440,9 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           double w0[3], w1[3], w2[3];
 #pragma unroll
           for (int t = 0; t < 3; ++t) {
-            w0[t] = __ldg(co + (n == 0 ? t * 3 : t) * P);
-            w1[t] = __ldg(co + (n == 0 ? t * 3 + 1 : 3 + t) * P);
-            w2[t] = __ldg(co + (n == 0 ? t * 3 + 2 : 6 + t) * P);
+            w0[t] = ldv<LD>(co + (n == 0 ? t * 3 : t) * P);
+            w1[t] = ldv<LD>(co + (n == 0 ? t * 3 + 1 : 3 + t) * P);
+            w2[t] = ldv<LD>(co + (n == 0 ? t * 3 + 2 : 6 + t) * P);
           }
           // overlapping trace at its centre line (normal coordinate 0)
           const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
@@ -548,7 +543,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     dp[2] = d2;
   }
   if (usig != nullptr) {
-    const double tau = dt[0];
+    const double tau = ldv<LD>(dt);
     const double r1 = d0 + d1, r2 = r1 + d2;
     const double e1 = exp(-tau * r1), e2 = exp(-tau * r2);
     double* os = usig + (long long)mesh * F * 9 * P + (long long)j * g.nx + i;
@@ -557,7 +552,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
 #pragma unroll
       for (int m = 0; m < 9; ++m) {
         const int deg = (m % 3) + (m / 3);
-        const double v = __ldg(us + (f * 9 + m) * P);
+        const double v = ldv<LD>(us + (f * 9 + m) * P);
         os[(f * 9 + m) * P] = deg == 0 ? v : (deg == 1 ? v * e1 : v * e2);
       }
     }

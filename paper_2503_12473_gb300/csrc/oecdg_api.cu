@@ -12,6 +12,7 @@
 #include "oecdg_common.cuh"
 #include "oecdg_ctx.h"
 #include "oecdg_kernels.h"
+#include "oecdg_persist.cuh"
 
 using namespace oecdg;
 
@@ -121,6 +122,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   ALLOC(avg, (size_t)2 * c->F * sizeof(double));
   ALLOC(status, sizeof(int));
 #undef ALLOC
+  c->wait_s = 5.0;
   e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, 2 * sizeof(double), c->stream);
@@ -152,6 +154,8 @@ cdg_status cdg_free(cdg_ctx* c) {
   cudaFree(c->sigma);
   cudaFree(c->avg);
   cudaFree(c->status);
+  cudaFree(c->p_wpart);
+  cudaFree(c->p_bar);
   prof_release(c);
   adj_release(c);
   free(c);
@@ -491,7 +495,72 @@ cdg_status cdg_check_status(cdg_ctx* ctx) {
   CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "check_status");
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "check_status");
   CK(cudaStreamSynchronize(ctx->stream), "check_status");
+  if (h & ST_TIMEOUT) return fail(ctx, CDG_ETIMEOUT, "a grid barrier of the persistent step ran out of time");
   if (h & ST_NONPHYSICAL) return fail(ctx, CDG_ENONPHYSICAL, "non-physical cell average (rho <= 0 or p <= 0)");
+  return CDG_OK;
+}
+
+cdg_status cdg_set_wait(cdg_ctx* ctx, double limit_s, int withheld) {
+  if (!ctx) return CDG_EINVAL;
+  if (!(limit_s > 0.0) || limit_s > 3600.0 || withheld < 0) return fail(ctx, CDG_EINVAL, "set_wait: bad arguments");
+  ctx->wait_s = limit_s;
+  ctx->withhold = withheld;
+  return CDG_OK;
+}
+
+cdg_status cdg_step_persistent(cdg_ctx* ctx, double* d_u, double t, double T_end, int nsteps) {
+  if (!ctx || !d_u) return fail(ctx, CDG_EINVAL, "step_persistent: null pointer");
+  if (nsteps < 0) return fail(ctx, CDG_EINVAL, "step_persistent: nsteps < 0");
+  if (ctx->d.dim != 1) return fail(ctx, CDG_EUNSUPPORTED, "step_persistent: 1D meshes only");
+  if (d_u == ctx->buf_a || d_u == ctx->buf_b || d_u == ctx->buf_c || d_u == ctx->buf_d)
+    return fail(ctx, CDG_EINVAL, "step_persistent: d_u is a context buffer");
+  if (!ctx->p_bar) {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev), "step_persistent");
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "step_persistent");
+    CK(persist_grid_1d(ctx->sys, ctx->bc, ctx->d.k, ctx->g, nsm, &ctx->p_grid), "step_persistent");
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)ctx->p_grid * sizeof(double)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(ctx, CDG_ENOMEM, "step_persistent: scratch");
+    }
+    ctx->p_wpart = (double*)p;
+    if (cudaMalloc(&p, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(ctx, CDG_ENOMEM, "step_persistent: scratch");
+    }
+    ctx->p_bar = (unsigned long long*)p;
+  }
+  CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step_persistent");
+  ctx->launches += 1;
+  if (nsteps == 0) return CDG_OK;
+  const int rk = ctx->d.rk, nst = n_stages(rk);
+  const double* U[4] = {d_u, ctx->buf_b, rk == CDG_RK_RK4 ? ctx->buf_c : ctx->buf_b,
+                        rk == CDG_RK_RK4 ? ctx->buf_d : ctx->buf_b};
+  Persist1 a = {};
+  for (int l = 0; l < nst; ++l) {
+    a.cb[l] = rk_comb(rk, l, U);
+    a.uin[l] = U[l];
+    a.dst[l] = l == nst - 1 ? d_u : (double*)U[l + 1];
+  }
+  a.ua = ctx->buf_a;
+  a.dt = ctx->dt;
+  a.time = ctx->time;
+  a.sigma = ctx->sigma;
+  a.avg = ctx->avg;
+  a.partials = ctx->partials;
+  a.wpart = ctx->p_wpart;
+  a.status = ctx->status;
+  a.nst = nst;
+  a.oe = ctx->d.oe;
+  a.nsteps = nsteps;
+  a.T_end = T_end;
+  a.nblk = ctx->nblk;
+  a.bar = ctx->p_bar;
+  a.expected = (unsigned long long)ctx->p_grid + (unsigned long long)ctx->withhold;
+  a.limit_ns = (unsigned long long)(ctx->wait_s * 1e9);
+  CK(launch_persist1d(ctx->sys, ctx->bc, ctx->d.k, ctx->g, a, ctx->p_grid, ctx->stream), "step_persistent");
+  ctx->launches += 1;
   return CDG_OK;
 }
 

@@ -9,7 +9,13 @@
 // would alone (bitwise, for the same tile height R = 4 as the single-mesh
 // kernels).  A step is 11 launches whatever the number of instances, and
 // cdg_batch_step can capture the launches of nsteps steps in a CUDA graph.
-// The tile height R (2, 4 or 8 rows) is picked by cdg_batch_autotune.
+// The persistent mode runs nsteps steps of every instance in ONE cooperative
+// launch (k_bpersist): its blocks loop over the same tiles phase by phase and
+// meet at grid-wide barriers with a bounded wait (CDG_ETIMEOUT when a wait
+// runs out); it runs the same per-cell code and the same fixed-order
+// reductions, so its results equal the per-phase launches' bit for bit.
+// The tile height R (2, 4 or 8 rows) and the persistent grid (blocks per SM)
+// are picked by cdg_batch_autotune.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -18,6 +24,7 @@
 #include "../../include/oecdg.h"
 #include "oecdg_2d_body.cuh"
 #include "oecdg_kernels.h"
+#include "oecdg_persist.cuh"
 
 namespace oecdg {
 
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(32 * R) k_bstage(const BatchInst* __restrict__
   const BatchInst& in = I[q];
   const int tiles = in.tx * in.ty;
   const int local = (int)(blk - in.blk0);
-  const int mesh = local / tiles, t = local - mesh * tiles;
+  const int mesh = local & 1, t = local >> 1;  // the two meshes' blocks of a tile side by side
   const int i = (t % in.tx) * 32 + (threadIdx.x & 31);
   const int j = (t / in.tx) * R + (threadIdx.x >> 5);
   stage_cell2d<SYS, BC, MODE_STAGE>(in.g, l == 0 ? in.u : in.b, in.u, in.a, in.dt, ca, cb,
@@ -70,9 +77,8 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
   const long long blk = blockIdx.x;
   const int q = find_instance(I, n, blk);
   const BatchInst& in = I[q];
-  const int tiles = in.tx * in.ty;
   const int local = (int)(blk - in.blk0);
-  const int mesh = local / tiles, t = local - mesh * tiles;
+  const int mesh = local & 1, t = local >> 1;
   const int i = (t % in.tx) * 32 + (threadIdx.x & 31);
   const int j = (t / in.tx) * R + (threadIdx.x >> 5);
   // square cells: the isotropic variant, as the single-mesh launch chooses it
@@ -82,44 +88,31 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
     oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
 }
 
-// avg and sigma per instance, mesh and field: grid (F, 2, n), fixed order
+// avg and sigma per instance, mesh and field: grid (F, 2, n), one warp each,
+// the fixed-order reduction shared with every other path
 __global__ void k_bsigma(const BatchInst* __restrict__ I, int F) {
-  const int f = blockIdx.x, mesh = blockIdx.y;
   const BatchInst& in = I[blockIdx.z];
-  const long long nblk = (long long)in.tx * in.ty;
-  __shared__ double sh[96];
-  double s = 0.0, mx = -DINF, mn = DINF;
-  for (long long b = threadIdx.x; b < nblk; b += blockDim.x) {
-    const double* p = in.part + ((mesh * nblk + b) * F + f) * 3;
-    s += p[0];
-    mx = fmax(mx, p[1]);
-    mn = fmin(mn, p[2]);
-  }
-  block_reduce3(s, mx, mn, sh);
-  if (threadIdx.x == 0) {
-    const double a = s / (double)in.g.plane;
-    in.avg[mesh * F + f] = a;
-    in.sigma[mesh * F + f] = fmax(mx - a, a - mn);
-  }
+  warp_sigma<LD_NC>(in.part, (long long)in.tx * in.ty, F, blockIdx.y, blockIdx.x, in.g.plane, in.avg, in.sigma);
 }
 
-// per-instance maximum wave speeds over both meshes' cell averages: grid (WB, n)
-template <int SYS>
-__global__ void k_bwave(const BatchInst* __restrict__ I, int* __restrict__ status) {
+// per-instance maximum wave speeds over both meshes' cell averages: chunk ch
+// of WB takes cells ch * blockDim.x + threadIdx.x, strided by WB * blockDim.x
+template <int SYS, int LD>
+__device__ __forceinline__ void bwave_chunk(const BatchInst& in, int ch, int* __restrict__ status) {
   constexpr int F = Fields<SYS>::F;
-  const BatchInst& in = I[blockIdx.y];
   const Geo& g = in.g;
   __shared__ double sh[32];
   const long long nc = 2 * g.plane;
   double mx = 0.0, my = 0.0;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+  for (long long c = (long long)ch * blockDim.x + threadIdx.x; c < nc; c += (long long)WB * blockDim.x) {
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
     const double* us = in.u + (long long)mesh * F * 9 * g.plane + cell;
     if (SYS == SYS_EULER) {
-      const double rho = us[0], m1 = us[9 * g.plane], m2 = us[18 * g.plane], E = us[27 * g.plane];
+      const double rho = ldv<LD>(us), m1 = ldv<LD>(us + 9 * g.plane), m2 = ldv<LD>(us + 18 * g.plane),
+                   E = ldv<LD>(us + 27 * g.plane);
       const double vx = m1 / rho, vy = m2 / rho;
-      const double p = (g.gamma - 1.0) * (E - 0.5 * (m1 * vx + m2 * vy));
+      const double p = (g.gamma - 1.0) * fma(-0.5, fma(m1, vx, m2 * vy), E);
       if (rho > 0.0 && p > 0.0) {
         const double cs = sqrt(g.gamma * p / rho);
         mx = fmax(mx, fabs(vx) + cs);
@@ -136,26 +129,111 @@ __global__ void k_bwave(const BatchInst* __restrict__ I, int* __restrict__ statu
   __syncthreads();
   my = block_reduce_max(my, sh);
   if (threadIdx.x == 0) {
-    in.wpart[blockIdx.x * 2] = mx;
-    in.wpart[blockIdx.x * 2 + 1] = my;
+    in.wpart[ch * 2] = mx;
+    in.wpart[ch * 2 + 1] = my;
   }
+  __syncthreads();  // sh is reused by the next chunk
 }
 
-// tau_max = C_CFL / (beta_x/h_x + beta_y/h_y) per instance (no end time)
-__global__ void k_bdt(const BatchInst* __restrict__ I, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const BatchInst& in = I[q];
+// grid (WB, n)
+template <int SYS>
+__global__ void k_bwave(const BatchInst* __restrict__ I, int* __restrict__ status) {
+  bwave_chunk<SYS, LD_NC>(I[blockIdx.y], blockIdx.x, status);
+}
+
+// tau_max of one instance from its WB wave partials (no end time): the time
+// step of Section 4, as finish_dt without clipping
+template <int LD>
+__device__ __forceinline__ void bdt_instance(const BatchInst& in) {
   double bx = 0.0, by = 0.0;
   for (int b = 0; b < WB; ++b) {
-    bx = fmax(bx, in.wpart[2 * b]);
-    by = fmax(by, in.wpart[2 * b + 1]);
+    bx = fmax(bx, ldv<LD>(in.wpart + 2 * b));
+    by = fmax(by, ldv<LD>(in.wpart + 2 * b + 1));
   }
   const double rate = bx / in.g.hx + by / in.g.hy;
   const double tm = rate > 0.0 ? in.g.cfl / rate : 0.0;
   in.dt[0] = tm;
   in.dt[1] = tm > 0.0 ? tm : 1.0;
-  in.time[0] += tm;
+  in.time[0] += tm;  // written only here, by the thread that owns instance q in every step
+}
+
+// tau_max = C_CFL / (beta_x/h_x + beta_y/h_y) per instance (no end time)
+__global__ void k_bdt(const BatchInst* __restrict__ I, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) bdt_instance<LD_NC>(I[q]);
+}
+
+// ------------------------------------------------------- persistent step --
+
+__constant__ double BSSP3_CA[3] = {0.0, 0.75, 1.0 / 3.0};
+
+struct BPersistArgs {
+  const BatchInst* I;
+  int n;
+  long long ntiles;             // tiles of all instances, both meshes (= the per-phase grid)
+  int nsteps;
+  unsigned long long* bar;      // barrier arrival counter, zeroed before the launch
+  unsigned long long expected;  // arrivals per barrier: gridDim.x (+ withheld ones in a test)
+  unsigned long long limit_ns;  // bounded wait of every barrier
+  int* status;
+  int stages;                   // 3 (the SSP-RK3 step); 1 when the autotuner times a first stage only
+};
+
+// nsteps SSP-RK3 steps of every instance in one cooperative launch.  Phases
+// (each ends at a grid barrier): wave-speed chunks (instance x WB) -> tau per
+// instance -> 3 x [stage tiles -> sigma (one warp per instance, mesh and
+// field) -> OE tiles].  Block b takes the items b, b + gridDim.x, ... of every
+// phase; data written in one phase are read in a later one with plain loads
+// (LD_CA), ordered by the barriers' fences.  A barrier that runs out of time
+// sets ST_TIMEOUT and every block returns.
+template <int SYS, int BC, int R>
+__global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
+  constexpr int F = Fields<SYS>::F;
+  const long long nwave = (long long)a.n * WB;
+  for (int s = 0; s < a.nsteps; ++s) {
+    for (long long it = blockIdx.x; it < nwave; it += gridDim.x)
+      bwave_chunk<SYS, LD_CA>(a.I[it / WB], (int)(it % WB), a.status);
+    if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.n;
+         q += (long long)gridDim.x * blockDim.x)
+      bdt_instance<LD_CA>(a.I[q]);
+    if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+    for (int l = 0; l < a.stages; ++l) {
+      const double ca = BSSP3_CA[l];
+      for (long long b = blockIdx.x; b < a.ntiles; b += gridDim.x) {
+        const BatchInst& in = a.I[find_instance(a.I, a.n, b)];
+        const int tiles = in.tx * in.ty;
+        const int local = (int)(b - in.blk0);
+        const int mesh = local & 1, t = local >> 1;
+        stage_cell2d<SYS, BC, MODE_STAGE, LD_CA>(in.g, l == 0 ? in.u : in.b, in.u, in.a, in.dt, ca, 1.0 - ca,
+                                                 in.part + ((long long)mesh * tiles + t) * F * 3, mesh,
+                                                 (t % in.tx) * 32 + (threadIdx.x & 31),
+                                                 (t / in.tx) * R + (threadIdx.x >> 5));
+      }
+      if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+      const int nw = blockDim.x >> 5;
+      for (long long it = (long long)blockIdx.x * nw + (threadIdx.x >> 5); it < (long long)a.n * 2 * F;
+           it += (long long)gridDim.x * nw) {
+        const BatchInst& in = a.I[it / (2 * F)];
+        const int mesh = (int)((it / F) & 1), f = (int)(it % F);
+        warp_sigma<LD_CA>(in.part, (long long)in.tx * in.ty, F, mesh, f, in.g.plane, in.avg, in.sigma);
+      }
+      if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+      for (long long b = blockIdx.x; b < a.ntiles; b += gridDim.x) {
+        const BatchInst& in = a.I[find_instance(a.I, a.n, b)];
+        const int local = (int)(b - in.blk0);
+        const int mesh = local & 1, t = local >> 1;
+        const int i = (t % in.tx) * 32 + (threadIdx.x & 31), j = (t / in.tx) * R + (threadIdx.x >> 5);
+        double* out = l == 2 ? in.u : in.b;
+        if (in.g.hx == in.g.hy)
+          oe_cell2d<SYS, BC, false, 0, true, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i, j);
+        else
+          oe_cell2d<SYS, BC, false, 0, false, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i,
+                                                     j);
+      }
+      if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
+    }
+  }
 }
 
 __global__ void k_bset_time(const BatchInst* __restrict__ I, int n, double t) {
@@ -182,7 +260,14 @@ struct cdg_batch {
   double** h_ptrs;         // the caller's state pointers last uploaded
   cudaGraphExec_t graph;
   int graph_steps;
+  int graph_flags;         // the cdg_batch_step flags the graph was captured with
   long long launches;
+  // persistent mode
+  unsigned long long* bar; // grid-barrier arrival counter (device)
+  int nsm;                 // SMs of the device
+  int bps;                 // persistent blocks per SM (0: as many as fit)
+  double wait_s;           // bounded wait of every grid barrier
+  int withhold;            // test hook: arrivals every barrier waits for that never come
   char err[256];
 };
 
@@ -257,12 +342,82 @@ static cudaError_t batch_one_step(cdg_batch* B) {
   for (int l = 0; l < 3; ++l) {
     const double ca = BSSP3_C[l];
     if ((e = launch_bstage(B, l, ca, 1.0 - ca)) != cudaSuccess) return e;
-    k_bsigma<<<dim3(B->F, 2, B->n), 1024, 0, B->stream>>>(B->d_inst, B->F);
+    k_bsigma<<<dim3(B->F, 2, B->n), 32, 0, B->stream>>>(B->d_inst, B->F);
     B->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_boe(B, l == 2)) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// One cooperative launch of nsteps steps (`stages` stages each, see
+// BPersistArgs); the arrival counter is zeroed first (a memset node when
+// captured).  Grid: blocks per SM x SMs, at most what fits and at most the
+// tiles.
+template <int BC, int R>
+static cudaError_t launch_bpersist_t(cdg_batch* B, int nsteps, int stages, long long* grid_out) {
+  auto kern = k_bpersist<SYS_EULER, BC, R>;
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * R, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int bps = (B->bps > 0 && B->bps < occ) ? B->bps : occ;
+  long long grid = (long long)bps * B->nsm;
+  if (grid > B->total_blocks) grid = B->total_blocks;
+  if (grid_out) *grid_out = grid;
+  BPersistArgs a;
+  a.I = B->d_inst;
+  a.n = B->n;
+  a.ntiles = B->total_blocks;
+  a.nsteps = nsteps;
+  a.bar = B->bar;
+  a.expected = (unsigned long long)grid + (unsigned long long)B->withhold;
+  a.limit_ns = (unsigned long long)(B->wait_s * 1e9);
+  a.status = B->status;
+  a.stages = stages;
+  if ((e = cudaMemsetAsync(B->bar, 0, sizeof(unsigned long long), B->stream)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(32 * R);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = B->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int BC>
+static cudaError_t launch_bpersist_bc(cdg_batch* B, int nsteps, int stages, long long* grid) {
+  switch (B->rows) {
+    case 2: return launch_bpersist_t<BC, 2>(B, nsteps, stages, grid);
+    case 8: return launch_bpersist_t<BC, 8>(B, nsteps, stages, grid);
+    default: return launch_bpersist_t<BC, 4>(B, nsteps, stages, grid);
+  }
+}
+
+static cudaError_t launch_bpersist(cdg_batch* B, int nsteps, int stages, long long* grid = nullptr) {
+  B->launches += 1;
+  if (B->bc == BC_PERIODIC) return launch_bpersist_bc<BC_PERIODIC>(B, nsteps, stages, grid);
+  return launch_bpersist_bc<BC_TRANSMISSIVE>(B, nsteps, stages, grid);
+}
+
+// blocks per SM of the persistent kernel that fit for tile height R
+static int persist_occupancy(const cdg_batch* B, int R) {
+  int occ = 0;
+  cudaError_t e;
+  if (B->bc == BC_PERIODIC)
+    e = R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_PERIODIC, 2>, 64, 0)
+        : R == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_PERIODIC, 8>, 256, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_PERIODIC, 4>, 128, 0);
+  else
+    e = R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_TRANSMISSIVE, 2>, 64, 0)
+        : R == 8
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_TRANSMISSIVE, 8>, 256, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<SYS_EULER, BC_TRANSMISSIVE, 4>, 128, 0);
+  return e == cudaSuccess ? occ : 0;
 }
 
 extern "C" {
@@ -308,9 +463,19 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
     const size_t tiles = (size_t)((d.nx + 31) / 32) * ((d.ny + 1) / 2);
     total += 2 * (size_t)2 * 4 * 9 * plane + 2 * tiles * 4 * 3 + WB * 2 + 2 + 2 + 8 + 8;
   }
+  B->wait_s = 5.0;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cdg_batch_free(B);
+      return CDG_ECUDA;
+    }
+  }
   if (cudaMalloc((void**)&B->pool, total * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&B->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
-      cudaMalloc((void**)&B->status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void**)&B->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&B->bar, sizeof(unsigned long long)) != cudaSuccess) {
     (void)cudaGetLastError();  // clear the failed allocation: later launch checks must not see it
     cdg_batch_free(B);
     return CDG_ENOMEM;
@@ -361,6 +526,7 @@ cdg_status cdg_batch_free(cdg_batch* B) {
   cudaFree(B->pool);
   cudaFree(B->d_inst);
   cudaFree(B->status);
+  cudaFree(B->bar);
   if (B->own_stream) cudaStreamDestroy(B->stream);
   free(B->h_inst);
   free(B->h_ptrs);
@@ -393,17 +559,22 @@ static cdg_status batch_bind(cdg_batch* B, double* const* d_us) {
   return CDG_OK;
 }
 
-cdg_status cdg_batch_step(cdg_batch* B, double* const* d_us, int nsteps, int use_graph) {
-  if (!B || !d_us || nsteps < 0) return bfail(B, CDG_EINVAL, "batch_step: bad arguments");
+cdg_status cdg_batch_step(cdg_batch* B, double* const* d_us, int nsteps, int flags) {
+  if (!B || !d_us || nsteps < 0 || flags < 0 || flags > 3) return bfail(B, CDG_EINVAL, "batch_step: bad arguments");
   cdg_status s = batch_bind(B, d_us);
   if (s != CDG_OK) return s;
   if (nsteps == 0) return CDG_OK;
+  const int use_graph = flags & CDG_BATCH_GRAPH, persist = flags & CDG_BATCH_PERSISTENT;
   if (!use_graph) {
+    if (persist) {
+      if (launch_bpersist(B, nsteps, 3) != cudaSuccess) return bfail(B, CDG_ECUDA, "batch_step: persistent launch failed");
+      return CDG_OK;
+    }
     for (int k = 0; k < nsteps; ++k)
       if (batch_one_step(B) != cudaSuccess) return bfail(B, CDG_ECUDA, "batch_step: launch failed");
     return CDG_OK;
   }
-  if (!B->graph || B->graph_steps != nsteps) {
+  if (!B->graph || B->graph_steps != nsteps || B->graph_flags != flags) {
     if (B->graph) {
       cudaGraphExecDestroy(B->graph);
       B->graph = nullptr;
@@ -413,7 +584,9 @@ cdg_status cdg_batch_step(cdg_batch* B, double* const* d_us, int nsteps, int use
       return bfail(B, CDG_ECUDA, "batch_step: stream capture failed to begin");
     cudaError_t e = cudaSuccess;
     const long long before = B->launches;  // captured launches are counted when the graph runs
-    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = batch_one_step(B);
+    if (persist) e = launch_bpersist(B, nsteps, 3);
+    else
+      for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = batch_one_step(B);
     B->launches = before;
     cudaError_t e2 = cudaStreamEndCapture(B->stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) return bfail(B, CDG_ECUDA, "batch_step: capture failed");
@@ -421,9 +594,47 @@ cdg_status cdg_batch_step(cdg_batch* B, double* const* d_us, int nsteps, int use
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bfail(B, CDG_ECUDA, "batch_step: graph instantiation failed");
     B->graph_steps = nsteps;
+    B->graph_flags = flags;
   }
   if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) return bfail(B, CDG_ECUDA, "batch_step: graph launch failed");
-  B->launches += 11LL * nsteps;
+  B->launches += persist ? 1 : 11LL * nsteps;
+  return CDG_OK;
+}
+
+cdg_status cdg_batch_set_wait(cdg_batch* B, double limit_s, int withheld) {
+  if (!B || !(limit_s > 0.0) || limit_s > 3600.0 || withheld < 0) return bfail(B, CDG_EINVAL, "batch_set_wait: bad arguments");
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return CDG_ECUDA;
+  B->wait_s = limit_s;
+  B->withhold = withheld;
+  if (B->graph) {  // the limits are baked into a captured launch
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    B->graph_steps = 0;
+  }
+  return CDG_OK;
+}
+
+cdg_status cdg_batch_set_grid(cdg_batch* B, int blocks_per_sm) {
+  if (!B || blocks_per_sm < 0) return bfail(B, CDG_EINVAL, "batch_set_grid: bad arguments");
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return CDG_ECUDA;
+  B->bps = blocks_per_sm;
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    B->graph_steps = 0;
+  }
+  return CDG_OK;
+}
+
+cdg_status cdg_batch_grid(const cdg_batch* B, int* blocks_per_sm, int* grid) {
+  if (!B || !blocks_per_sm || !grid) return CDG_EINVAL;
+  const int occ = persist_occupancy(B, B->rows);
+  if (occ < 1) return CDG_ECUDA;
+  const int bps = (B->bps > 0 && B->bps < occ) ? B->bps : occ;
+  long long g = (long long)bps * B->nsm;
+  if (g > B->total_blocks) g = B->total_blocks;
+  *blocks_per_sm = bps;
+  *grid = (int)g;
   return CDG_OK;
 }
 
@@ -434,6 +645,7 @@ cdg_status cdg_batch_check_status(cdg_batch* B) {
       cudaMemsetAsync(B->status, 0, sizeof(int), B->stream) != cudaSuccess ||
       cudaStreamSynchronize(B->stream) != cudaSuccess)
     return bfail(B, CDG_ECUDA, "batch_check_status: CUDA error");
+  if (h & ST_TIMEOUT) return bfail(B, CDG_ETIMEOUT, "a grid barrier of the persistent kernel ran out of time");
   if (h & ST_NONPHYSICAL) return bfail(B, CDG_ENONPHYSICAL, "non-physical cell average in the batch");
   return CDG_OK;
 }
@@ -485,8 +697,7 @@ static int cache_lookup(const char* path, const char* sig) {
   snprintf(key, sizeof key, "\"%s\": ", sig);
   const char* p = strstr(buf, key);
   if (!p) return 0;
-  int r = atoi(p + strlen(key));
-  return (r == 2 || r == 4 || r == 8) ? r : 0;
+  return atoi(p + strlen(key));
 }
 
 static void cache_store(const char* path, const char* sig, int rows) {
@@ -522,40 +733,61 @@ cdg_status cdg_batch_autotune(cdg_batch* B, double* const* d_us, const char* cac
   if (s != CDG_OK) return s;
   char sig[128];
   batch_signature(B, sig, sizeof sig);
-  int best = cache_path ? cache_lookup(cache_path, sig) : 0;
-  if (!best) {
-    // time one stage + sigma + OE of every candidate (reads the states, writes
-    // only the scratch buffers), best of 3
-    const int cand[3] = {2, 4, 8};
+  // cache code: rows * 100 + blocks per SM (a bare 2, 4 or 8: rows only)
+  const int code = cache_path ? cache_lookup(cache_path, sig) : 0;
+  int best_rows = 0, best_bps = 0;
+  if (code == 2 || code == 4 || code == 8) {
+    best_rows = code;
+  } else if (code >= 100) {
+    const int r = code / 100, b = code % 100;
+    if ((r == 2 || r == 4 || r == 8) && b >= 0 && b <= persist_occupancy(B, r)) {
+      best_rows = r;
+      best_bps = b;
+    }
+  }
+  if (!best_rows) {
+    // time the persistent kernel on one first stage of every instance (wave
+    // speeds, tau, stage, sigma, OE into scratch: the caller's states are only
+    // read) for every tile height and every persistent grid that fits; best of
+    // two after a warm-up
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CDG_ECUDA;
-    k_bwave<SYS_EULER><<<dim3(WB, B->n), 256, 0, B->stream>>>(B->d_inst, B->status);
-    k_bdt<<<(B->n + 127) / 128, 128, 0, B->stream>>>(B->d_inst, B->n);
-    k_bset_time<<<(B->n + 127) / 128, 128, 0, B->stream>>>(B->d_inst, B->n, 0.0);
+    const int saved_bps = B->bps;
+    const int cand[3] = {2, 4, 8};
     for (int c = 0; c < 3; ++c) {
       if (batch_layout(B, cand[c]) != cudaSuccess) return CDG_ECUDA;
-      for (int rep = 0; rep < 4; ++rep) {
-        cudaEventRecord(e0, B->stream);
-        launch_bstage(B, 0, 0.0, 1.0);
-        k_bsigma<<<dim3(B->F, 2, B->n), 1024, 0, B->stream>>>(B->d_inst, B->F);
-        launch_boe(B, 0);
-        cudaEventRecord(e1, B->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) return CDG_ECUDA;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0 && ms < best_ms) {
-          best_ms = ms;
-          best = cand[c];
+      const int occ = persist_occupancy(B, cand[c]);
+      for (int bps = 1; bps <= occ; ++bps) {
+        B->bps = bps;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, B->stream);
+          if (launch_bpersist(B, 1, 1) != cudaSuccess) return bfail(B, CDG_ECUDA, "autotune: launch failed");
+          cudaEventRecord(e1, B->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) return bfail(B, CDG_ECUDA, "autotune: kernel failed");
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0 && ms < best_ms) {
+            best_ms = ms;
+            best_rows = cand[c];
+            best_bps = bps;
+          }
         }
       }
     }
+    B->bps = saved_bps;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (cache_path) cache_store(cache_path, sig, best);
+    k_bset_time<<<(B->n + 127) / 128, 128, 0, B->stream>>>(B->d_inst, B->n, 0.0);
+    B->launches += 1;
+    int h = 0;  // a timed-out candidate leaves its bit: report it rather than a choice
+    if (cudaMemcpy(&h, B->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CDG_ECUDA;
+    if (h & ST_TIMEOUT) return bfail(B, CDG_ETIMEOUT, "autotune: a grid barrier ran out of time");
+    if (cache_path) cache_store(cache_path, sig, best_rows * 100 + best_bps);
   }
-  if (batch_layout(B, best) != cudaSuccess) return CDG_ECUDA;
-  if (rows_out) *rows_out = best;
+  if (batch_layout(B, best_rows) != cudaSuccess) return CDG_ECUDA;
+  B->bps = best_bps;
+  if (rows_out) *rows_out = best_rows;
   return CDG_OK;
 }
 

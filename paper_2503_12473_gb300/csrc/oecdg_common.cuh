@@ -89,12 +89,15 @@ struct Geo {
   double cfl;
 };
 
-// 2D Euler flux components at a conserved state (rho, mx, my, E).
+// 2D Euler flux components at a conserved state (rho, mx, my, E).  Every
+// multiply-add is an explicit fma: the compiler's own contraction may differ
+// between the kernels that inline these (single-mesh, batched, persistent,
+// recording), whose results must agree bit for bit.
 struct Euler2 {
   __device__ static __forceinline__ void both(const double* w, double g, double* f1, double* f2) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
     const double H = w[3] + p;
     f1[0] = w[1];
     f1[1] = fma(w[1], vx, p);
@@ -108,7 +111,7 @@ struct Euler2 {
   __device__ static __forceinline__ void fx(const double* w, double g, double* f1) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
     f1[0] = w[1];
     f1[1] = fma(w[1], vx, p);
     f1[2] = w[2] * vx;
@@ -117,7 +120,7 @@ struct Euler2 {
   __device__ static __forceinline__ void fy(const double* w, double g, double* f2) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * (w[3] - 0.5 * (w[1] * vx + w[2] * vy));
+    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
     f2[0] = w[2];
     f2[1] = w[1] * vy;
     f2[2] = fma(w[2], vy, p);

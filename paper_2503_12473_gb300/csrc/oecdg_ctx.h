@@ -45,6 +45,12 @@ struct cdg_ctx {
   int prof_n[2];
   cudaEvent_t* prof_ev[2];  // [class][2 * cap]: start, stop
   struct AdjScratch* adj;   // adjoint buffers, allocated by the first cdg_step_adjoint
+  // persistent step (cdg_step_persistent): allocated by its first call
+  double* p_wpart;          // one wave-speed partial per persistent block
+  unsigned long long* p_bar;  // grid-barrier arrival counter
+  long long p_grid;         // blocks of the persistent grid
+  double wait_s;            // bounded wait of every grid barrier (cdg_set_wait)
+  int withhold;             // test hook: arrivals that never come
   char err[256];
 };
 

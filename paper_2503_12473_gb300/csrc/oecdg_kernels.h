@@ -37,6 +37,28 @@ cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* p
 cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st);
 cudaError_t launch_project1d(int sys, int k, const Geo& g, const double* vals, double* u, cudaStream_t st);
 
+// Persistent 1D step: nsteps steps of Eq. (eq:RKCDG) in one cooperative launch
+// (oecdg_1d.cu).  Stage l evaluates L at uin[l], combines cb[l] into ua, and
+// the OE step (or a copy without OE) writes dst[l].
+struct Persist1 {
+  StageComb cb[4];
+  const double* uin[4];
+  double* dst[4];
+  double* ua;
+  double *dt, *time, *sigma, *avg, *partials, *wpart;
+  int* status;
+  int nst, oe, nsteps;
+  double T_end;
+  long long nblk;               // stage blocks per mesh (partials layout)
+  unsigned long long* bar;      // [barrier arrivals, last-block tickets], zeroed before the launch
+  unsigned long long expected;  // arrivals per barrier (the grid, plus withheld ones in a test)
+  unsigned long long limit_ns;  // bounded wait of every barrier
+};
+// blocks of the persistent grid: as many as fit on the device, at most the tiles
+cudaError_t persist_grid_1d(int sys, int bc, int k, const Geo& g, int nsm, long long* grid);
+cudaError_t launch_persist1d(int sys, int bc, int k, const Geo& g, const Persist1& a, long long grid,
+                             cudaStream_t st);
+
 // 2D Q^k / P^k, k in {1, 2, 3}: every configuration outside the tiled Q^2 path
 long long partial_blocks_2k(const Geo& g);
 int modes_2k(int k, int basis);

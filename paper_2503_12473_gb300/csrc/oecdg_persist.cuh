@@ -1,0 +1,142 @@
+// oecdg_persist.cuh -- pieces shared by the persistent (cooperative) kernels:
+// a grid-wide barrier with a bounded wait, coherent loads for data written
+// earlier in the same launch, and the fixed-order sigma reduction that every
+// path (per-phase launches and persistent kernels) runs, so that their
+// results agree bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "oecdg_common.cuh"
+
+namespace oecdg {
+
+// Status bit of a grid barrier that gave up waiting (CDG_ETIMEOUT on the host).
+enum { ST_TIMEOUT = 2 };
+
+// Load policy of the per-cell bodies.  LD_NC: the read-only (non-coherent)
+// path, valid when nothing the kernel reads is written during the launch (one
+// launch per phase).  LD_CA: plain (coherent, L1-cached) loads, for persistent
+// kernels, whose phases read what earlier phases of the same launch wrote: the
+// grid barrier's fences order those writes before the reads (the read-only
+// path is outside that guarantee).  LD_CG: cached in L2 only.
+enum { LD_NC = 0, LD_CA = 1, LD_CG = 2 };
+
+template <int LD>
+__device__ __forceinline__ double ldv(const double* p) {
+  if (LD == LD_NC) return __ldg(p);
+  if (LD == LD_CG) return __ldcg(p);
+  return *p;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  `count` is a 64-bit arrival
+// counter, zero at launch; the k-th barrier completes when it reaches
+// k * expected (expected = gridDim.x, or more to make the wait run out on
+// purpose in a test).  Thread 0 of each block publishes the block's writes
+// (__syncthreads, then a device-scope fence before its arrival: release),
+// spins with a short sleep until the barrier completes, until another block
+// has given up (the status word has ST_TIMEOUT), or until limit_ns of its own
+// wait have passed, when it sets ST_TIMEOUT; then a device-scope fence
+// (acquire) and __syncthreads order the block's later loads after every
+// block's writes.  Returns false after a timeout: the caller then leaves the
+// kernel, so every block ends within about one limit.
+__device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long expected, int* status,
+                                          unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long arrive = atomicAdd(count, 1ULL);
+    const unsigned long long target = (arrive / expected + 1) * expected;
+    const unsigned long long t0 = global_ns();
+    int good = 1;
+    while (*(volatile unsigned long long*)count < target) {
+      if (*(volatile int*)status & ST_TIMEOUT) {
+        good = 0;
+        break;
+      }
+      if (global_ns() - t0 > limit_ns) {
+        atomicOr(status, ST_TIMEOUT);
+        good = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// True in exactly one block per call: the last of gridDim.x blocks to finish
+// the phase that precedes the call (a monotone ticket counter, zero at
+// launch).  That block then sees every other block's writes of the phase
+// (release fence before each ticket, acquire fence after the last one).
+__device__ __forceinline__ bool last_block(unsigned long long* tickets) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long t = atomicAdd(tickets, 1ULL);
+    last = (t + 1) % gridDim.x == 0;
+    if (last) __threadfence();
+  }
+  __syncthreads();
+  return last != 0;
+}
+
+// avg and sigma of one (mesh, field) from the block partials [2][nblk][F][3]
+// (sum of cell averages, max, min), by one full warp in a fixed order: lane l
+// folds partials l, l + 32, ...; then a shuffle tree.  avg = sum / ncell,
+// sigma = max(max - avg, avg - min) (Section 2.2, sigma_K).
+template <int LD>
+__device__ __forceinline__ void warp_sigma(const double* part, long long nblk, int F, int mesh, int f,
+                                           long long ncell, double* avg, double* sigma) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double s = 0.0, mx = -__builtin_huge_val(), mn = __builtin_huge_val();
+  for (long long b = lane; b < nblk; b += 32) {
+    const double* p = part + ((mesh * nblk + b) * F + f) * 3;
+    s += ldv<LD>(p);
+    mx = fmax(mx, ldv<LD>(p + 1));
+    mn = fmin(mn, ldv<LD>(p + 2));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(full, s, o);
+    mx = fmax(mx, __shfl_down_sync(full, mx, o));
+    mn = fmin(mn, __shfl_down_sync(full, mn, o));
+  }
+  if (lane == 0) {
+    const double a = s / (double)ncell;
+    avg[mesh * F + f] = a;
+    sigma[mesh * F + f] = fmax(mx - a, a - mn);
+  }
+}
+
+// tau_max = C_CFL / (beta_x/h_x + beta_y/h_y) (1D: C_CFL h / beta) from the
+// maxima bx, by; tau = tau_max clipped at T_end > 0 (a step that would leave a
+// sliver shorter than 1e-12 T_end is stretched to T_end); time[0] advances.
+__device__ __forceinline__ void finish_dt(double bx, double by, double hx, double hy, int dim, double cfl,
+                                          double T_end, double* dt, double* time) {
+  const double rate = bx / hx + (dim == 2 ? by / hy : 0.0);
+  const double tm = rate > 0.0 ? cfl / rate : 0.0;
+  const double t = time[0];
+  double tau = tm;
+  if (T_end > 0.0) {
+    if (t >= T_end) tau = 0.0;
+    else if (T_end - (t + tm) < 1e-12 * T_end) tau = T_end - t;
+  }
+  dt[0] = tau;
+  dt[1] = tm > 0.0 ? tm : 1.0;
+  time[0] = (T_end > 0.0 && tau == T_end - t) ? T_end : t + tau;
+}
+
+}  // namespace oecdg

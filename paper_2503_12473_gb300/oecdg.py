@@ -21,6 +21,7 @@ BASIS_Q, BASIS_P = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 RK_EULER1, RK_SSP2, RK_SSP3, RK_RK4 = 1, 2, 3, 4
 MATH_RCP, MATH_SQRT = 0, 1
+BATCH_GRAPH, BATCH_PERSISTENT = 1, 2
 
 STATUS_NAMES = {0: "CDG_OK", 1: "CDG_EINVAL", 2: "CDG_ENOMEM", 3: "CDG_ECUDA", 4: "CDG_ENONPHYSICAL",
                 5: "CDG_ETIMEOUT", 6: "CDG_EUNSUPPORTED"}
@@ -34,6 +35,7 @@ EXPORTED = [
     "cdg_batch_get_time", "cdg_batch_launch_count", "cdg_batch_rows", "cdg_batch_autotune",
     "cdg_step_adjoint", "cdg_batch_set_rows", "cdg_record_numel", "cdg_step_record", "cdg_step_adjoint_recorded",
     "cdg_rk_combine", "cdg_step_graph", "cdg_math_eval",
+    "cdg_batch_set_wait", "cdg_batch_set_grid", "cdg_batch_grid", "cdg_step_persistent", "cdg_set_wait",
 ]
 
 
@@ -109,6 +111,10 @@ def load(build_if_missing: bool = True):
     L.cdg_step_async.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.cdg_step_graph.restype = st
     L.cdg_step_graph.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.cdg_step_persistent.restype = st
+    L.cdg_step_persistent.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.cdg_set_wait.restype = st
+    L.cdg_set_wait.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.cdg_get_time.restype = st
     L.cdg_get_time.argtypes = [vp, dp]
     L.cdg_check_status.restype = st
@@ -142,6 +148,12 @@ def load(build_if_missing: bool = True):
     L.cdg_batch_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.cdg_batch_autotune.restype = st
     L.cdg_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+    L.cdg_batch_set_wait.restype = st
+    L.cdg_batch_set_wait.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.cdg_batch_set_grid.restype = st
+    L.cdg_batch_set_grid.argtypes = [vp, ctypes.c_int]
+    L.cdg_batch_grid.restype = st
+    L.cdg_batch_grid.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.cdg_launch_count.restype = st
     L.cdg_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.cdg_step_adjoint.restype = st
@@ -347,6 +359,12 @@ class Context:
     def cdg_step_graph(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
         self._ck(self._L.cdg_step_graph(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_graph")
 
+    def cdg_step_persistent(self, d_u, t: float = 0.0, T_end: float = 0.0, nsteps: int = 1):
+        self._ck(self._L.cdg_step_persistent(self.h, _ptr(d_u), t, T_end, nsteps), "cdg_step_persistent")
+
+    def cdg_set_wait(self, limit_s: float, withheld: int = 0):
+        self._ck(self._L.cdg_set_wait(self.h, ctypes.c_double(limit_s), withheld), "cdg_set_wait")
+
     def cdg_step_adjoint(self, d_un, d_lam_next, d_lam, d_gtau=None):
         self._ck(self._L.cdg_step_adjoint(self.h, _ptr(d_un), _ptr(d_lam_next), _ptr(d_lam), _ptr(d_gtau)),
                  "cdg_step_adjoint")
@@ -447,9 +465,22 @@ class Batch:
         except Exception:
             pass
 
-    def cdg_batch_step(self, states, nsteps: int = 1, use_graph: bool = False):
+    def cdg_batch_step(self, states, nsteps: int = 1, use_graph: bool = False, persistent: bool = False):
         self._keep = self._ptrs(states)
-        self._ck(self._L.cdg_batch_step(self.h, self._keep, nsteps, int(bool(use_graph))), "cdg_batch_step")
+        flags = (BATCH_GRAPH if use_graph else 0) | (BATCH_PERSISTENT if persistent else 0)
+        self._ck(self._L.cdg_batch_step(self.h, self._keep, nsteps, flags), "cdg_batch_step")
+
+    def cdg_batch_set_wait(self, limit_s: float, withheld: int = 0):
+        self._ck(self._L.cdg_batch_set_wait(self.h, ctypes.c_double(limit_s), withheld), "cdg_batch_set_wait")
+
+    def cdg_batch_set_grid(self, blocks_per_sm: int):
+        self._ck(self._L.cdg_batch_set_grid(self.h, blocks_per_sm), "cdg_batch_set_grid")
+
+    def cdg_batch_grid(self):
+        """(blocks per SM, total blocks) of the persistent grid."""
+        b, g = ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.cdg_batch_grid(self.h, ctypes.byref(b), ctypes.byref(g)), "cdg_batch_grid")
+        return b.value, g.value
 
     def cdg_batch_check_status(self) -> int:
         return self._L.cdg_batch_check_status(self.h)

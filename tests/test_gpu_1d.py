@@ -314,3 +314,109 @@ def test_pk_orders_1d(case, k):
         errs.append(float(np.sum(np.abs(v - ex(x, t)) * wq / 2)) / n)
     rate = math.log2(errs[0] / errs[1])
     assert rate > k + 0.5, (errs, rate)
+
+
+PERSIST_CASES = [("advection", W.ADVECTION, 2, 3, 1), ("shu-osher", W.EULER, 2, 3, 1), ("euler-p3-rk4", W.EULER, 3, 4, 1),
+                 ("burgers-p1-ssp2", W.BURGERS, 1, 2, 1), ("burgers-p2-euler1", W.BURGERS, 2, 1, 1),
+                 ("advection-no-oe", W.ADVECTION, 3, 3, 0)]
+
+
+def _same_to_rounding(a, b, tol=1e-13):
+    """max |a - b| / max |b| per field (the fields' scales differ)."""
+    num = (a - b).abs().amax(dim=(0, 2, 3, 4))
+    den = b.abs().amax(dim=(0, 2, 3, 4)).clamp_min(1e-300)
+    return (num / den).max().item() <= tol
+
+
+@pytest.mark.parametrize("name,sys,k,rk,oe", PERSIST_CASES)
+def test_step_persistent_equals_step(name, sys, k, rk, oe):
+    """cdg_step_persistent (all steps in one cooperative launch, grid-wide
+    barriers between the phases) gives cdg_step_async's result to rounding
+    (1 ulp differences appear at discontinuities: the two kernels are compiled
+    separately, and their quadrature constants and multiply-adds may round
+    differently), and the same time: every system, degree and RK method of the
+    1D path, with and without OE, periodic and transmissive, including the
+    clipped last step at T_end and the skipped steps after it.  Its runs are
+    deterministic (bitwise repeatable)."""
+    from paper_2503_12473_gb300 import oecdg as G
+    if name == "advection":
+        w = W.advection_1d(128)
+    elif name == "shu-osher":
+        w = W.shu_osher_1d(4000)
+    else:
+        w = _wl(sys, k, rk, 300)
+    w = W.Workload(w.name, 1, w.nx, 1, k, sys, w.bc, w.ax, w.bx, adv=w.adv, cfl=w.cfl, rk=rk, oe=oe, u0=w.u0)
+    # the context on torch's current stream: the copies below and the steps are ordered
+    ctx = G.Context(G.desc_from_workload(w))
+    u0 = ctx.project(w.u0)
+    a = u0.clone()
+    b = u0.clone()
+    # a short end time: the last of n steps is clipped, the rest skipped on the device
+    ctx.cdg_step_async(a, 0.0, 0.0, 1)
+    tau, _ = ctx.cdg_get_dt()
+    T = 37.5 * tau
+    n = 45
+    ctx.cdg_step_async(a.copy_(u0), 0.0, T, n)
+    ta = ctx.cdg_get_time()
+    assert ctx.cdg_check_status() == G.CDG_OK
+    ctx.cdg_step_persistent(b, 0.0, T, n)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert ctx.cdg_get_time() == ta
+    assert _same_to_rounding(b, a)
+    c = u0.clone()
+    ctx.cdg_step_persistent(c, 0.0, T, n)
+    assert torch.equal(b, c)  # deterministic
+    # and without an end time, in two calls
+    ctx.cdg_step_async(a.copy_(u0), 0.0, 0.0, 12)
+    ctx.cdg_step_persistent(b.copy_(u0), 0.0, 0.0, 5)
+    ctx.cdg_step_persistent(b, ctx.cdg_get_time(), 0.0, 7)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert _same_to_rounding(b, a)
+    ctx.cdg_step_persistent(c.copy_(u0), 0.0, 0.0, 12)
+    assert torch.equal(b, c)  # two launches of 5 + 7 steps equal one of 12
+
+
+def test_step_persistent_barrier_wait_runs_out_without_hanging():
+    """The grid barriers' waits are bounded.  With the test hook that makes
+    every barrier wait for one arrival that never comes, the launch ends by
+    itself after about the limit and cdg_check_status reports CDG_ETIMEOUT;
+    nothing faults, and the context then steps normally again."""
+    import time
+    from paper_2503_12473_gb300 import oecdg as G
+    w = W.shu_osher_1d(4000)
+    ctx = G.Context(G.desc_from_workload(w))
+    u0 = ctx.project(w.u0)
+    a = u0.clone()
+    b = u0.clone()
+    ctx.cdg_set_wait(0.2, withheld=1)
+    t0 = time.time()
+    ctx.cdg_step_persistent(b, 0.0, 0.0, 3)
+    assert ctx.cdg_check_status() == G.CDG_ETIMEOUT
+    assert time.time() - t0 < 10.0
+    ctx.cdg_set_wait(5.0, withheld=0)
+    ctx.cdg_step_async(a, 0.0, 0.0, 3)
+    ctx.cdg_step_persistent(b.copy_(u0), 0.0, 0.0, 3)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    assert _same_to_rounding(b, a)
+    with pytest.raises(G.CdgError) as e:
+        ctx.cdg_set_wait(0.0)
+    assert e.value.status == G.CDG_EINVAL
+
+
+def test_step_persistent_against_oracle():
+    """The persistent launch against the oracle: 1D Euler Shu-Osher data, P^2,
+    4000 cells, 100 steps (rel L1 <= 1e-9 per field, the bar for
+    discontinuous runs), and 1D advection of sin x over its whole period
+    (1280 steps, <= 1e-11)."""
+    from paper_2503_12473_gb300 import oecdg as G
+    for w, n, T, tol in ((W.shu_osher_1d(4000), 100, 0.0, 1e-9), (W.advection_1d(128), 1300, 2 * math.pi, 1e-11)):
+        ctx = G.Context(G.desc_from_workload(w))
+        p = _oracle_problem(w)
+        uo = O.project_fn(p, w.u0)
+        ug = torch.from_numpy(uo).cuda()
+        ctx.cdg_step_persistent(ug, 0.0, T, n)
+        assert ctx.cdg_check_status() == G.CDG_OK
+        ref, t, steps, status = O.advance(p, uo, 0.0, T, n)
+        assert status == O.OK
+        assert abs(ctx.cdg_get_time() - t) <= 1e-13 * max(t, 1.0)
+        assert rel_l1(ug.cpu().numpy(), ref).max() < tol, (w.name, rel_l1(ug.cpu().numpy(), ref))

@@ -104,11 +104,17 @@ def test_tile_heights_and_autotune(batch_setup, tmp_path):
     b = G.Batch(descs)
     rows = b.cdg_batch_autotune(u0, cache)
     assert rows in (2, 4, 8)
+    bps, grid = b.cdg_batch_grid()
+    assert bps >= 1 and grid >= 1
     data = json.load(open(cache))
-    assert list(data.values()) == [rows]
-    assert G.Batch(descs).cdg_batch_autotune(u0, cache) == rows  # from the cache
+    assert list(data.values()) == [rows * 100 + bps]  # tile height and persistent grid
+    b2 = G.Batch(descs)
+    assert b2.cdg_batch_autotune(u0, cache) == rows  # from the cache
+    assert b2.cdg_batch_grid() == (bps, grid)
+    for u, v in zip(u0, _initial(G, descs, ics)):  # the tuner only read the states
+        assert torch.equal(u, v)
     us = [u.clone() for u in u0]
-    b.cdg_batch_step(us, 1)
+    b.cdg_batch_step(us, 1, persistent=True)
     assert b.cdg_batch_check_status() == G.CDG_OK  # synchronises the batch's stream
     for u, r in zip(us, ref):
         # other tile heights sum the sigma partials in another order
@@ -131,3 +137,56 @@ def test_batched_oracle_parity(batch_setup):
         got = u.cpu().numpy()
         err = np.abs(got - ref).sum(axis=(0, 2, 3, 4)) / np.abs(ref).sum(axis=(0, 2, 3, 4))
         assert err.max() < 1e-9, err
+
+
+@pytest.mark.parametrize("rows", [2, 4, 8])
+def test_persistent_equals_per_phase_launches(batch_setup, rows):
+    """One cooperative launch for all steps (grid-wide barriers between the
+    phases) gives the per-phase launches' results bit for bit, directly and
+    captured in a CUDA graph, for every tile height and for a persistent grid
+    smaller than the tile count (blocks loop over several tiles)."""
+    G, descs, ics = batch_setup
+    u0 = _initial(G, descs, ics)
+    b = G.Batch(descs)
+    b.cdg_batch_set_rows(rows)
+    ref = [u.clone() for u in u0]
+    b.cdg_batch_step(ref, 3)
+    assert b.cdg_batch_check_status() == G.CDG_OK
+    t_ref = b.cdg_batch_get_time()
+    for graph, bps in ((False, 0), (True, 0), (False, 1)):
+        bp = G.Batch(descs, stream=torch.cuda.Stream())
+        bp.cdg_batch_set_rows(rows)
+        bp.cdg_batch_set_grid(bps)
+        us = [u.clone() for u in u0]
+        bp.cdg_batch_step(us, 3, use_graph=graph, persistent=True)
+        assert bp.cdg_batch_check_status() == G.CDG_OK
+        for u, r in zip(us, ref):
+            assert torch.equal(u, r), (rows, graph, bps)
+        np.testing.assert_array_equal(bp.cdg_batch_get_time(), t_ref)
+        assert bp.cdg_batch_launch_count() == 1
+
+
+def test_persistent_barrier_wait_runs_out_without_hanging(batch_setup):
+    """The grid barriers' waits are bounded.  With the test hook that makes
+    every barrier wait for one arrival that never comes, the launch ends by
+    itself after about the limit and reports CDG_ETIMEOUT; nothing faults, and
+    the same batch then steps normally again (from a restored state)."""
+    import time
+    G, descs, ics = batch_setup
+    u0 = _initial(G, descs, ics)
+    ref = [u.clone() for u in u0]
+    G.Batch(descs).cdg_batch_step(ref, 2)
+    torch.cuda.synchronize()
+    b = G.Batch(descs)
+    b.cdg_batch_set_wait(0.2, withheld=1)
+    us = [u.clone() for u in u0]
+    t0 = time.time()
+    b.cdg_batch_step(us, 2, persistent=True)
+    assert b.cdg_batch_check_status() == G.CDG_ETIMEOUT
+    assert time.time() - t0 < 10.0
+    b.cdg_batch_set_wait(5.0, withheld=0)
+    us = [u.clone() for u in u0]
+    b.cdg_batch_step(us, 2, persistent=True)
+    assert b.cdg_batch_check_status() == G.CDG_OK
+    for u, r in zip(us, ref):
+        assert torch.equal(u, r)
