@@ -27,6 +27,13 @@
  *   - the dual mesh is the primal mesh shifted by (+hx/2, +hy/2), with the same
  *     number of cells; transmissive boundaries: a ghost cell outside the stored
  *     range is a copy of the nearest stored cell (all modes), per direction;
+ *   - reflective walls (Euler): the restriction of the mirror-extended problem.
+ *     Beyond a wall the solution is the mirror image of the inside (normal
+ *     momentum negated); the dual mesh gains the cell centred on a low-side wall
+ *     (stored in the slot after the last cell, so that both meshes keep the
+ *     same padded layout); sigma and avg are those of the mirror-extended
+ *     domain (wall-centred dual cells count half, a normal momentum has
+ *     average 0);
  *   - quadrature: (k+1)-point Gauss-Legendre per direction on every sub-cell and
  *     half-face; Legendre polynomials unnormalised (P_n(1) = 1);
  *   - tau_max is the CFL value at the start of the step (maximum wave speed over
@@ -78,7 +85,7 @@ typedef double real;
 
 enum { ORC_ADVECTION = 0, ORC_BURGERS = 1, ORC_EULER = 2 };
 enum { ORC_BASIS_Q = 0, ORC_BASIS_P = 1 };
-enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1 };
+enum { ORC_PERIODIC = 0, ORC_TRANSMISSIVE = 1, ORC_REFLECTIVE = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENONPHYSICAL = 4 };
 
 /* Problem description (mirrored by a ctypes.Structure in oracle/oracle.py). */
@@ -88,10 +95,10 @@ typedef struct {
   int k;       /* polynomial degree, 0..3 */
   int basis;   /* ORC_BASIS_Q (tensor Q^k) or ORC_BASIS_P (total degree P^k) */
   int system;  /* ORC_ADVECTION, ORC_BURGERS, ORC_EULER */
-  int bc;      /* ORC_PERIODIC or ORC_TRANSMISSIVE (same on every side) */
+  int bc[4];   /* per side: x-low, x-high, y-low, y-high (1D: x only); ORC_PERIODIC
+                  (on both sides of a direction), ORC_TRANSMISSIVE or ORC_REFLECTIVE */
   int oe;      /* 1: apply the OE step after every stage */
   int rk;      /* 1 forward Euler, 2 SSP-RK2, 3 SSP-RK3, 4 classical RK4 */
-  int pad;
   double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
   double gamma;          /* ratio of specific heats (Euler) */
   double adv_x, adv_y;   /* advection velocity */
@@ -128,11 +135,25 @@ static int nmodes(const orc_problem* p) {
 static double hx_of(const orc_problem* p) { return (p->bx - p->ax) / p->nx; }
 static double hy_of(const orc_problem* p) { return p->dim == 2 ? (p->by - p->ay) / p->ny : 1.0; }
 
+/* 1 if side s (0: x-low, 1: x-high, 2: y-low, 3: y-high) is a reflective wall. */
+static int refl(const orc_problem* p, int s) { return (p->dim == 2 || s < 2) && p->bc[s] == ORC_REFLECTIVE; }
+
+/* Stored cells per direction of the padded layout (both meshes): nx, plus the
+ * slot of the dual cell centred on a reflective low-side wall. */
+static int nxs(const orc_problem* p) { return p->nx + refl(p, 0); }
+static int nys(const orc_problem* p) { return p->dim == 2 ? p->ny + refl(p, 2) : 1; }
+/* cells of mesh `mesh` per direction (the primal mesh leaves the slot unused) */
+static int ncx(const orc_problem* p, int mesh) { return mesh == 0 ? p->nx : nxs(p); }
+static int ncy(const orc_problem* p, int mesh) { return mesh == 0 ? (p->dim == 2 ? p->ny : 1) : nys(p); }
+
 /* Index of coefficient (mesh, field, mode, j, i) in the state array. */
 static size_t sidx(const orc_problem* p, int mesh, int f, int m, int j, int i) {
   int F = nfields(p), M = nmodes(p);
-  return ((((size_t)mesh * F + f) * M + m) * p->ny + j) * (size_t)p->nx + i;
+  return ((((size_t)mesh * F + f) * M + m) * nys(p) + j) * (size_t)nxs(p) + i;
 }
+
+/* Doubles in a state array (2 meshes x fields x modes x the padded cells). */
+static size_t state_len(const orc_problem* p) { return (size_t)2 * nfields(p) * nmodes(p) * nys(p) * nxs(p); }
 
 /* d-th derivative of the Legendre polynomial P_n at x (unnormalised, P_n(1)=1).
  * Three-term recurrence for the values and P^{(d)}_{n+1} = P^{(d)}_{n-1} +
@@ -173,40 +194,69 @@ void orc_gauss(int n, double* x, double* w) {
  * [x_i, x_{i+1}] between primal centres, i.e. it is centred on primal vertex i+1. */
 static void cell_centre(const orc_problem* p, int mesh, int i, int j, double* xc, double* yc) {
   double hx = hx_of(p), hy = hy_of(p);
-  *xc = p->ax + (i + 0.5 + 0.5 * mesh) * hx;
-  *yc = p->dim == 2 ? p->ay + (j + 0.5 + 0.5 * mesh) * hy : 0.0;
+  /* the slot after the last dual cell holds the cell centred on the low wall */
+  int iu = (mesh == 1 && i == p->nx) ? -1 : i, ju = (mesh == 1 && j == p->ny) ? -1 : j;
+  *xc = p->ax + (iu + 0.5 + 0.5 * mesh) * hx;
+  *yc = p->dim == 2 ? p->ay + (ju + 0.5 + 0.5 * mesh) * hy : 0.0;
 }
 
-/* Map an unwrapped cell index to a stored one: periodic wrap, or the
- * transmissive ghost convention (ghost cell := copy of the nearest stored cell,
- * every mode copied; corners by composition).  The paper does not say how the
- * dual mesh is closed at an outflow boundary.  Pinned where an outflow
- * boundary is fixed by the physics: while the flow beside the boundary is
- * uniform in the normal direction, a run equals the run on an enlarged domain
- * cell for cell (tests/test_oracle_transmissive.py); the zeroth-order
- * extrapolation beyond that is a convention. */
-static int store_index(const orc_problem* p, int iu, int n) {
-  if (p->bc == ORC_PERIODIC) return ((iu % n) + n) % n;
-  return iu < 0 ? 0 : (iu >= n ? n - 1 : iu);
+/* Map an unwrapped cell index of direction `dir` (cell iu of the primal mesh
+ * spans [iu h, (iu+1) h], dual cell iu is centred on vertex iu + 1) to a stored
+ * one; *mirror = 1 when the cell is the mirror image of the stored cell across
+ * a reflective wall.
+ *   periodic: wrap;
+ *   transmissive: the ghost cell outside the stored range is a copy of the
+ *     nearest stored cell, every mode copied (corners by composition).  The
+ *     paper does not say how the dual mesh is closed at an outflow boundary.
+ *     Pinned where an outflow boundary is fixed by the physics: while the flow
+ *     beside the boundary is uniform in the normal direction, a run equals the
+ *     run on an enlarged domain cell for cell (tests/test_oracle_transmissive.py);
+ *     the zeroth-order extrapolation beyond that is a convention;
+ *   reflective: the dual cell centred on a low wall (vertex 0) is a stored cell
+ *     (slot n); cells beyond a wall are mirror images: primal -1 - iu across the
+ *     low wall and 2n - 1 - iu across the high one, dual (vertex v -> -v, 2n - v).
+ *     Pinned: a reflective run equals the mirror-extended periodic run
+ *     (tests/test_oracle_reflective.py). */
+static int store_index(const orc_problem* p, int dir, int mesh, int iu, int* mirror) {
+  int n = dir == 0 ? p->nx : p->ny;
+  int lo = p->bc[2 * dir], hi = p->bc[2 * dir + 1];
+  *mirror = 0;
+  if (iu >= 0 && iu < n) return iu;
+  if (lo == ORC_PERIODIC) return ((iu % n) + n) % n;
+  if (iu < 0) {
+    if (lo == ORC_TRANSMISSIVE) return 0;
+    if (mesh == 1 && iu == -1) return n; /* the wall-centred dual cell */
+    *mirror = 1;
+    iu = mesh == 0 ? -1 - iu : -iu - 2;
+  } else {
+    if (hi == ORC_TRANSMISSIVE) return n - 1;
+    *mirror = 1;
+    iu = mesh == 0 ? 2 * n - 1 - iu : 2 * n - iu - 2;
+  }
+  return iu < 0 ? 0 : (iu >= n ? n - 1 : iu); /* one cell deep is all the scheme reads */
 }
 
 /* Locate the cell of mesh `mesh` containing the physical point (x, y) and give
- * the stored index and the point's reference coordinates in that cell. */
+ * the stored index, the point's reference coordinates in that cell and whether
+ * the cell is a mirror image in x / y (the coordinate is then mirrored too). */
 static void locate(const orc_problem* p, int mesh, double x, double y, int* si, int* sj, double* xi,
-                   double* eta) {
+                   double* eta, int* mirx, int* miry) {
   double hx = hx_of(p), hy = hy_of(p);
   int iu = (int)floor((x - p->ax) / hx - 0.5 * mesh);
   double xc = p->ax + (iu + 0.5 + 0.5 * mesh) * hx;
   *xi = (x - xc) / (0.5 * hx);
-  *si = store_index(p, iu, p->nx);
+  *si = store_index(p, 0, mesh, iu, mirx);
+  if (*mirx) *xi = -*xi;
   if (p->dim == 2) {
     int ju = (int)floor((y - p->ay) / hy - 0.5 * mesh);
     double yc = p->ay + (ju + 0.5 + 0.5 * mesh) * hy;
     *eta = (y - yc) / (0.5 * hy);
-    *sj = store_index(p, ju, p->ny);
+    *sj = store_index(p, 1, mesh, ju, miry);
+    if (*miry) *eta = -*eta;
   } else {
     *eta = 0.0;
     *sj = 0;
+    *miry = 0;
   }
 }
 
@@ -232,12 +282,28 @@ static void cell_eval(const orc_problem* p, const real* u, int mesh, int i, int 
   }
 }
 
+/* cell_eval of a located cell: for a mirror image across a wall normal to x
+ * (resp. y), the x-momentum (resp. y-momentum) changes sign and so does every
+ * odd-order x- (resp. y-) derivative: g(x) = S u(2 x_w - x). */
+static void located_eval(const orc_problem* p, const real* u, int mesh, int si, int sj, double xi, double eta,
+                         int mirx, int miry, int dx, int dy, real* out) {
+  cell_eval(p, u, mesh, si, sj, xi, eta, dx, dy, out);
+  if (!mirx && !miry) return;
+  int F = nfields(p);
+  for (int f = 0; f < F; ++f) {
+    int neg = 0;
+    if (mirx) neg ^= (dx & 1) ^ (p->system == ORC_EULER && f == 1);
+    if (miry) neg ^= (dy & 1) ^ (p->system == ORC_EULER && f == 2);
+    if (neg) out[f] = -out[f];
+  }
+}
+
 /* Value of the mesh-`mesh` solution at a physical point. */
 static void point_eval(const orc_problem* p, const real* u, int mesh, double x, double y, real* out) {
-  int si, sj;
+  int si, sj, mx, my;
   double xi, eta;
-  locate(p, mesh, x, y, &si, &sj, &xi, &eta);
-  cell_eval(p, u, mesh, si, sj, xi, eta, 0, 0, out);
+  locate(p, mesh, x, y, &si, &sj, &xi, &eta, &mx, &my);
+  located_eval(p, u, mesh, si, sj, xi, eta, mx, my, 0, 0, out);
 }
 
 /* ----------------------------------------------------------------- flux --- */
@@ -373,9 +439,10 @@ void orc_rhs(const orc_problem* p, const real* u, real tau_max, real* L) {
   int F = nfields(p), M = nmodes(p);
   real inv = 1.0 / tau_max;
   for (int mesh = 0; mesh < 2; ++mesh) {
+    int cy = ncy(p, mesh), cx = ncx(p, mesh);
 #pragma omp parallel for collapse(2) schedule(static)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
+    for (int j = 0; j < cy; ++j)
+      for (int i = 0; i < cx; ++i) {
         real Lc[ORC_MAXF * ORC_MAXM];
         cell_rhs(p, u, inv, mesh, i, j, Lc);
         for (int f = 0; f < F; ++f)
@@ -391,7 +458,7 @@ double orc_bilinear(const orc_problem* p, const double* u, const double* phi, do
   int F = nfields(p), M = nmodes(p);
   int ma[ORC_MAXM], mb[ORC_MAXM];
   modes(p, ma, mb);
-  size_t n = (size_t)2 * F * M * p->ny * p->nx;
+  size_t n = state_len(p);
   double* L = (double*)malloc(n * sizeof(double));
   orc_rhs(p, u, tau_max, L);
   double hx = hx_of(p), hy = hy_of(p), s = 0.0;
@@ -399,8 +466,8 @@ double orc_bilinear(const orc_problem* p, const double* u, const double* phi, do
     for (int f = 0; f < F; ++f)
       for (int m = 0; m < M; ++m) {
         double nrm = hx / (2.0 * ma[m] + 1.0) * (p->dim == 2 ? hy / (2.0 * mb[m] + 1.0) : 1.0);
-        for (int j = 0; j < p->ny; ++j)
-          for (int i = 0; i < p->nx; ++i) {
+        for (int j = 0; j < ncy(p, mesh); ++j)
+          for (int i = 0; i < ncx(p, mesh); ++i) {
             size_t id = sidx(p, mesh, f, m, j, i);
             s += nrm * L[id] * phi[id];
           }
@@ -412,41 +479,67 @@ double orc_bilinear(const orc_problem* p, const double* u, const double* phi, do
 
 /* --------------------------------------------------------- OE procedure --- */
 
+/* Weight of a cell of mesh `mesh` in the domain average: 1, halved for each
+ * reflective wall the cell is centred on (dual cells only: the mirror-extended
+ * domain holds such a cell once, every other cell twice). */
+static double cell_weight(const orc_problem* p, int mesh, int i, int j) {
+  if (mesh == 0) return 1.0;
+  double w = 1.0;
+  if ((refl(p, 0) && i == p->nx) || (refl(p, 1) && i == p->nx - 1)) w *= 0.5;
+  if (p->dim == 2 && ((refl(p, 2) && j == p->ny) || (refl(p, 3) && j == p->ny - 1))) w *= 0.5;
+  return w;
+}
+
+/* 1 if field f changes sign in the mirror image across a reflective wall (the
+ * normal momentum): its average over the mirror-extended domain is 0. */
+static int odd_field(const orc_problem* p, int f) {
+  if (p->system != ORC_EULER) return 0;
+  return (f == 1 && (refl(p, 0) || refl(p, 1))) || (p->dim == 2 && f == 2 && (refl(p, 2) || refl(p, 3)));
+}
+
 /* Global scales of one mesh, per field (Section 2.2, definition of sigma_K):
  *   avg(u) = (1/|Omega|) int_Omega u   (cell Gauss rule, stored cells only),
  *   sigma  = || u - avg(u) ||_{L^inf}, the max taken over the (k+1)^d Gauss
- *            points of every stored cell (parity unpinned: a convention). */
+ *            points of every stored cell (parity unpinned: a convention).
+ * With reflective walls Omega is the mirror-extended domain: wall-centred dual
+ * cells count half in the average, a normal momentum has average 0 (its mirror
+ * image is its negative), and the max of |u - avg| over the mirror images
+ * equals that over the stored cells. */
 static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg, real* sig) {
   int F = nfields(p), nq = p->k + 1, d = p->dim;
   double gx[ORC_MAXQ], gw[ORC_MAXQ];
   orc_gauss(nq, gx, gw);
   double hx = hx_of(p), hy = hy_of(p);
   int nqy = d == 2 ? nq : 1;
+  int cy = ncy(p, mesh), cx = ncx(p, mesh);
   /* fixed summation order: each row of cells in sequence, then the rows in
    * sequence (the rows may be summed by different threads) */
-  real* rows = (real*)calloc((size_t)p->ny * (F + 1), sizeof(real));
+  real* rows = (real*)calloc((size_t)cy * (F + 1), sizeof(real));
 #pragma omp parallel for schedule(static)
-  for (int j = 0; j < p->ny; ++j) {
+  for (int j = 0; j < cy; ++j) {
     real v[ORC_MAXF];
     real* r = rows + (size_t)j * (F + 1);
-    for (int i = 0; i < p->nx; ++i)
+    for (int i = 0; i < cx; ++i) {
+      double wc = cell_weight(p, mesh, i, j);
       for (int qy = 0; qy < nqy; ++qy)
         for (int qx = 0; qx < nq; ++qx) {
           double W = 0.5 * gw[qx] * hx * (d == 2 ? 0.5 * gw[qy] * hy : 1.0);
+          if (wc != 1.0) W *= wc;
           cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
           for (int f = 0; f < F; ++f) r[f] += W * v[f];
           r[F] += W;
         }
+    }
   }
   real vol = 0.0;
   real tot[ORC_MAXF] = {0};
-  for (int j = 0; j < p->ny; ++j) {
+  for (int j = 0; j < cy; ++j) {
     for (int f = 0; f < F; ++f) tot[f] += rows[(size_t)j * (F + 1) + f];
     vol += rows[(size_t)j * (F + 1) + F];
   }
   free(rows);
   for (int f = 0; f < F; ++f) {
-    avg[f] = tot[f] / vol;
+    avg[f] = odd_field(p, f) ? 0.0 : tot[f] / vol;
     sig[f] = 0.0;
   }
   /* the max of |u - avg| over all points (order-independent) */
@@ -455,8 +548,8 @@ static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg,
     real loc[ORC_MAXF] = {0};
     real v[ORC_MAXF];
 #pragma omp for schedule(static)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i)
+    for (int j = 0; j < cy; ++j)
+      for (int i = 0; i < cx; ++i)
         for (int qy = 0; qy < nqy; ++qy)
           for (int qx = 0; qx < nq; ++qx) {
             cell_eval(p, u, mesh, i, j, gx[qx], d == 2 ? gx[qy] : 0.0, 0, 0, v);
@@ -519,16 +612,16 @@ static int cell_delta(const orc_problem* p, const real* u, int mesh, int i, int 
           double xi = dir == 0 ? side : t, eta = dir == 0 ? t : side;
           double W = d == 2 ? 0.5 * gw[q] * 0.5 * elen : 1.0;
           double x = xc + 0.5 * hx * xi, y = yc + 0.5 * hy * eta;
-          int si, sj;
+          int si, sj, mx, my;
           double oxi, oeta;
-          locate(p, other, x, y, &si, &sj, &oxi, &oeta);
+          locate(p, other, x, y, &si, &sj, &oxi, &oeta, &mx, &my);
           real sq[ORC_MAXF] = {0};
           for (int ax = 0; ax <= m; ++ax) {
             int ay = m - ax;
             if (d == 1 && ay > 0) continue;
             real a1[ORC_MAXF], a2[ORC_MAXF];
             cell_eval(p, u, mesh, i, j, xi, d == 2 ? eta : 0.0, ax, ay, a1);
-            cell_eval(p, u, other, si, sj, oxi, oeta, ax, ay, a2);
+            located_eval(p, u, other, si, sj, oxi, oeta, mx, my, ax, ay, a2);
             for (int f = 0; f < F; ++f) {
               real df = mesh == 0 ? a1[f] - a2[f] : a2[f] - a1[f]; /* u^C - u^D */
               sq[f] += df * df;
@@ -551,7 +644,7 @@ static int cell_delta(const orc_problem* p, const real* u, int mesh, int i, int 
 }
 
 /* sigma and avg of both meshes (out arrays [2][F]) and delta of every cell
- * ([2][ny][nx][k+1]).  Returns ORC_ENONPHYSICAL if any cell average is not a
+ * ([2][ny][nx][k+1] in the padded layout of the state).  Returns ORC_ENONPHYSICAL if any cell average is not a
  * physical state. */
 int orc_oe_coefficients(const orc_problem* p, const real* u, real* delta, real* sigma, real* avg) {
   int F = nfields(p), K1 = p->k + 1;
@@ -564,12 +657,13 @@ int orc_oe_coefficients(const orc_problem* p, const real* u, real* delta, real* 
       if (avg) avg[mesh * F + f] = a[f];
     }
     int bad = 0;
+    int cy = ncy(p, mesh), cx = ncx(p, mesh);
 #pragma omp parallel for collapse(2) schedule(static) reduction(| : bad)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
+    for (int j = 0; j < cy; ++j)
+      for (int i = 0; i < cx; ++i) {
         real dl[ORC_MAXQ];
         if (cell_delta(p, u, mesh, i, j, s, dl) != ORC_OK) bad = 1;
-        for (int m = 0; m < K1; ++m) delta[(((size_t)mesh * p->ny + j) * p->nx + i) * K1 + m] = dl[m];
+        for (int m = 0; m < K1; ++m) delta[(((size_t)mesh * nys(p) + j) * nxs(p) + i) * K1 + m] = dl[m];
       }
     if (bad) status = ORC_ENONPHYSICAL;
   }
@@ -641,9 +735,9 @@ void orc_oe_apply(const orc_problem* p, const real* delta, real tau, real* u) {
   int ma[ORC_MAXM], mb[ORC_MAXM];
   int M = modes(p, ma, mb), F = nfields(p), K1 = p->k + 1;
   for (int mesh = 0; mesh < 2; ++mesh)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
-        const real* dl = delta + (((size_t)mesh * p->ny + j) * p->nx + i) * K1;
+    for (int j = 0; j < ncy(p, mesh); ++j)
+      for (int i = 0; i < ncx(p, mesh); ++i) {
+        const real* dl = delta + (((size_t)mesh * nys(p) + j) * nxs(p) + i) * K1;
         for (int m = 1; m < M; ++m) {
           real fac = oe_factor(p, dl, ma[m] + mb[m], tau);
           for (int f = 0; f < F; ++f) u[sidx(p, mesh, f, m, j, i)] *= fac;
@@ -655,8 +749,8 @@ void orc_oe_apply(const orc_problem* p, const real* delta, real tau, real* u) {
  * damp and (2k-1) < 0, so the step is the identity there. */
 int orc_oe(const orc_problem* p, real* u, real tau) {
   if (p->k == 0) return ORC_OK;
-  size_t nd = (size_t)2 * p->ny * p->nx * (p->k + 1);
-  real* delta = (real*)malloc(nd * sizeof(real));
+  size_t nd = (size_t)2 * nys(p) * nxs(p) * (p->k + 1);
+  real* delta = (real*)calloc(nd, sizeof(real));
   int st = orc_oe_coefficients(p, u, delta, NULL, NULL);
   orc_oe_apply(p, delta, tau, u);
   free(delta);
@@ -674,8 +768,8 @@ int orc_tau_max(const orc_problem* p, const real* u, real* tau_max) {
   real bxm = 0.0, bym = 0.0;
   int st = ORC_OK;
   for (int mesh = 0; mesh < 2; ++mesh)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
+    for (int j = 0; j < ncy(p, mesh); ++j)
+      for (int i = 0; i < ncx(p, mesh); ++i) {
         real w[ORC_MAXF];
         for (int f = 0; f < F; ++f) w[f] = u[sidx(p, mesh, f, 0, j, i)];
         real sx = wave_speed(p, w, 1.0, 0.0);
@@ -699,9 +793,8 @@ static void axpy_stage(size_t n, real* out, const real* a, double ca, const real
 /* One full time step of Eq. (eq:RKCDG) in place: the stages of the chosen RK
  * method, each followed by the OE step F_tau (if enabled). */
 int orc_step_tau(const orc_problem* p, real* u, real tau, real tau_max) {
-  int F = nfields(p), M = nmodes(p);
-  size_t n = (size_t)2 * F * M * p->ny * p->nx;
-  real* L = (real*)malloc(n * sizeof(real));
+  size_t n = state_len(p);
+  real* L = (real*)calloc(n, sizeof(real)); /* the primal mesh's padding slots stay 0 */
   real* u1 = (real*)malloc(n * sizeof(real));
   real* u2 = (real*)malloc(n * sizeof(real));
   real* u3 = (real*)malloc(n * sizeof(real));
@@ -791,30 +884,57 @@ int orc_advance(const orc_problem* p, real* u, double* t, double T_end, int nste
 #ifndef ORC_COMPLEX_STEP
 /* ------------------------------------------------- initial projection --- */
 
+/* A sampling point outside a reflective wall (the outer half of a
+ * wall-centred dual cell) is folded back to its mirror image inside; *mx, *my
+ * say whether it was (the initial data there is the mirror image of the data
+ * inside: the normal momentum changes sign). */
+static void fold_point(const orc_problem* p, double* x, double* y, int* mx, int* my) {
+  *mx = *my = 0;
+  if (refl(p, 0) && *x < p->ax) { *x = 2.0 * p->ax - *x; *mx = 1; }
+  if (refl(p, 1) && *x > p->bx) { *x = 2.0 * p->bx - *x; *mx = 1; }
+  if (p->dim == 2) {
+    if (refl(p, 2) && *y < p->ay) { *y = 2.0 * p->ay - *y; *my = 1; }
+    if (refl(p, 3) && *y > p->by) { *y = 2.0 * p->by - *y; *my = 1; }
+  }
+}
+
+/* Physical sampling point (qx, qy) of sub-cell (sx, sy) of cell (i, j). */
+static void sample_point(const orc_problem* p, int mesh, int i, int j, int sx, int sy, int qx, int qy,
+                         const double* gx, double* x, double* y) {
+  double xc, yc;
+  cell_centre(p, mesh, i, j, &xc, &yc);
+  double xi = sx - 0.5 + 0.5 * gx[qx];
+  double eta = sy - 0.5 + 0.5 * gx[qy];
+  *x = xc + 0.5 * hx_of(p) * xi;
+  *y = p->dim == 2 ? yc + 0.5 * hy_of(p) * eta : 0.0;
+}
+
 /* Composite Gauss points for sampling the initial data: on every stored cell
- * of both meshes, (k+1)^d Gauss points on each of its 2^d sub-cells.  Layout:
- * [mesh][j][i][sy][sx][qy][qx] with (x, y) pairs (1D: x only, layout
- * [mesh][i][sx][qx]).  Returns the number of points. */
+ * of both meshes (the padded layout: the primal mesh's unused slots get the
+ * points of the matching dual cell, whose values are ignored), (k+1)^d Gauss
+ * points on each of its 2^d sub-cells, points beyond a reflective wall folded
+ * back inside.  Layout: [mesh][j][i][sy][sx][qy][qx] with (x, y) pairs (1D: x
+ * only, layout [mesh][i][sx][qx]).  Returns the number of points. */
 size_t orc_quad_points(const orc_problem* p, double* xy) {
   int nq = p->k + 1, d = p->dim;
   double gx[ORC_MAXQ], gw[ORC_MAXQ];
   orc_gauss(nq, gx, gw);
-  double hx = hx_of(p), hy = hy_of(p);
   size_t n = 0;
   for (int mesh = 0; mesh < 2; ++mesh)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
-        double xc, yc;
-        cell_centre(p, mesh, i, j, &xc, &yc);
+    for (int j = 0; j < nys(p); ++j)
+      for (int i = 0; i < nxs(p); ++i) {
+        int cm = (i < ncx(p, mesh) && j < ncy(p, mesh)) ? mesh : 1; /* padding: any valid cell */
         for (int sy = 0; sy < (d == 2 ? 2 : 1); ++sy)
           for (int sx = 0; sx < 2; ++sx)
             for (int qy = 0; qy < (d == 2 ? nq : 1); ++qy)
               for (int qx = 0; qx < nq; ++qx) {
-                double xi = sx - 0.5 + 0.5 * gx[qx];
-                double eta = sy - 0.5 + 0.5 * gx[qy];
                 if (xy) {
-                  xy[n * d] = xc + 0.5 * hx * xi;
-                  if (d == 2) xy[n * d + 1] = yc + 0.5 * hy * eta;
+                  double x, y;
+                  int mx, my;
+                  sample_point(p, cm, i, j, sx, sy, qx, qy, gx, &x, &y);
+                  fold_point(p, &x, &y, &mx, &my);
+                  xy[n * d] = x;
+                  if (d == 2) xy[n * d + 1] = y;
                 }
                 ++n;
               }
@@ -833,9 +953,9 @@ void orc_project(const orc_problem* p, const double* vals, double* u) {
   orc_gauss(nq, gx, gw);
   int per_cell = (d == 2 ? 4 : 2) * (d == 2 ? nq * nq : nq);
   for (int mesh = 0; mesh < 2; ++mesh)
-    for (int j = 0; j < p->ny; ++j)
-      for (int i = 0; i < p->nx; ++i) {
-        size_t base = (((size_t)mesh * p->ny + j) * p->nx + i) * per_cell;
+    for (int j = 0; j < ncy(p, mesh); ++j)
+      for (int i = 0; i < ncx(p, mesh); ++i) {
+        size_t base = (((size_t)mesh * nys(p) + j) * nxs(p) + i) * per_cell;
         double acc[ORC_MAXF][ORC_MAXM];
         memset(acc, 0, sizeof acc);
         size_t n = 0;
@@ -847,9 +967,18 @@ void orc_project(const orc_problem* p, const double* vals, double* u) {
                 double eta = sy - 0.5 + 0.5 * gx[qy];
                 /* reference-square weights: the sub-cell has half the width */
                 double W = 0.5 * gw[qx] * (d == 2 ? 0.5 * gw[qy] : 1.0);
+                /* a point folded back across a wall carries the mirror image */
+                double x, y;
+                int mx, my;
+                sample_point(p, mesh, i, j, sx, sy, qx, qy, gx, &x, &y);
+                fold_point(p, &x, &y, &mx, &my);
                 for (int m = 0; m < M; ++m) {
                   double ph = orc_legendre(ma[m], 0, xi) * (d == 2 ? orc_legendre(mb[m], 0, eta) : 1.0);
-                  for (int f = 0; f < F; ++f) acc[f][m] += W * vals[(base + n) * F + f] * ph;
+                  for (int f = 0; f < F; ++f) {
+                    double v = vals[(base + n) * F + f];
+                    if (p->system == ORC_EULER && ((mx && f == 1) || (my && f == 2))) v = -v;
+                    acc[f][m] += W * v * ph;
+                  }
                 }
                 ++n;
               }
@@ -868,11 +997,24 @@ void orc_project(const orc_problem* p, const double* vals, double* u) {
 void orc_eval_cells(const orc_problem* p, const double* u, int mesh, int nq, const double* xi,
                     const double* eta, double* out) {
   int F = nfields(p);
-  for (int j = 0; j < p->ny; ++j)
-    for (int i = 0; i < p->nx; ++i)
+  for (int j = 0; j < ncy(p, mesh); ++j)
+    for (int i = 0; i < ncx(p, mesh); ++i)
       for (int q = 0; q < nq; ++q)
         cell_eval(p, u, mesh, i, j, xi[q], p->dim == 2 ? eta[q] : 0.0, 0, 0,
-                  out + ((((size_t)j * p->nx + i) * nq + q) * F));
+                  out + ((((size_t)j * nxs(p) + i) * nq + q) * F));
+}
+
+/* 0 if the problem description is valid, ORC_EINVAL otherwise: periodic on
+ * both sides of a direction or on neither, reflective walls for the Euler
+ * equations only (a wall reflects a velocity). */
+int orc_check(const orc_problem* p) {
+  for (int dir = 0; dir < p->dim; ++dir) {
+    int lo = p->bc[2 * dir], hi = p->bc[2 * dir + 1];
+    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return ORC_EINVAL;
+    if ((lo == ORC_PERIODIC) != (hi == ORC_PERIODIC)) return ORC_EINVAL;
+    if ((lo == ORC_REFLECTIVE || hi == ORC_REFLECTIVE) && p->system != ORC_EULER) return ORC_EINVAL;
+  }
+  return ORC_OK;
 }
 
 /* Evaluate the mesh-`mesh` solution at arbitrary physical points (located). */

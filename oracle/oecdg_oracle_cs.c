@@ -29,7 +29,7 @@
  * own loops then run on that thread).  Returns ORC_ENONPHYSICAL if any run
  * met a non-physical cell average. */
 int orc_step_jacobian(const orc_problem* p, const double* u, int nsteps, double h, double* J) {
-  const long n = (long)2 * nfields(p) * nmodes(p) * p->ny * p->nx;
+  const long n = (long)state_len(p);
   int bad = 0;
 #ifdef _OPENMP
   omp_set_max_active_levels(1);

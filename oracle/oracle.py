@@ -25,15 +25,15 @@ _LIB_CS = os.path.join(_BUILD, "liboecdg_oracle_cs.so")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
-PERIODIC, TRANSMISSIVE = 0, 1
+PERIODIC, TRANSMISSIVE, REFLECTIVE = 0, 1, 2
 OK, EINVAL, ENONPHYSICAL = 0, 1, 4
 
 
 class _Problem(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("k", ctypes.c_int),
-        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int), ("oe", ctypes.c_int),
-        ("rk", ctypes.c_int), ("pad", ctypes.c_int),
+        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int * 4), ("oe", ctypes.c_int),
+        ("rk", ctypes.c_int),
         ("ax", ctypes.c_double), ("bx", ctypes.c_double), ("ay", ctypes.c_double), ("by", ctypes.c_double),
         ("gamma", ctypes.c_double), ("adv_x", ctypes.c_double), ("adv_y", ctypes.c_double),
         ("cfl", ctypes.c_double),
@@ -93,6 +93,8 @@ def lib():
         L.orc_rhs_cells.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ip, dp]
         L.orc_oe_cells.restype = ctypes.c_int
         L.orc_oe_cells.argtypes = [P, dp, ctypes.c_double, ctypes.c_int, ip, dp, dp, dp, dp]
+        L.orc_check.restype = ctypes.c_int
+        L.orc_check.argtypes = [P]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib_handle = L
@@ -126,10 +128,30 @@ class Problem:
     cfl: float = 0.1
     _c: _Problem = field(default=None, repr=False, compare=False)
 
+    @property
+    def sides(self):
+        """Boundary condition of each side: (x-low, x-high, y-low, y-high)."""
+        b = self.bc
+        return tuple(b) if isinstance(b, (tuple, list)) else (b, b, b, b)
+
     def c(self) -> _Problem:
         ny = self.ny if self.dim == 2 else 1
-        return _Problem(self.dim, self.nx, ny, self.k, self.basis, self.system, self.bc, self.oe, self.rk, 0,
-                        self.ax, self.bx, self.ay, self.by, self.gamma, self.adv_x, self.adv_y, self.cfl)
+        pc = _Problem(self.dim, self.nx, ny, self.k, self.basis, self.system, (ctypes.c_int * 4)(*self.sides),
+                      self.oe, self.rk, self.ax, self.bx, self.ay, self.by, self.gamma, self.adv_x, self.adv_y,
+                      self.cfl)
+        if lib().orc_check(ctypes.byref(pc)) != OK:
+            raise ValueError(f"invalid boundary conditions {self.sides} for system {self.system}")
+        return pc
+
+    @property
+    def nxs(self) -> int:
+        """Stored cells per row: nx, plus the slot of the dual cell centred on a
+        reflective x-low wall (both meshes share this padded layout)."""
+        return self.nx + (self.sides[0] == REFLECTIVE)
+
+    @property
+    def nys(self) -> int:
+        return (self.ny + (self.sides[2] == REFLECTIVE)) if self.dim == 2 else 1
 
     @property
     def nfields(self) -> int:
@@ -153,8 +175,7 @@ class Problem:
 
     @property
     def shape(self):
-        ny = self.ny if self.dim == 2 else 1
-        return (2, self.nfields, self.nmodes, ny, self.nx)
+        return (2, self.nfields, self.nmodes, self.nys, self.nxs)
 
     @property
     def hx(self) -> float:
@@ -198,8 +219,7 @@ def bilinear(p: Problem, u: np.ndarray, phi: np.ndarray, tau_max: float) -> floa
 def oe_coefficients(p: Problem, u: np.ndarray):
     """(delta [2,ny,nx,k+1], sigma [2,F], avg [2,F], status)."""
     u = np.ascontiguousarray(u, dtype=np.float64)
-    ny = p.ny if p.dim == 2 else 1
-    delta = np.zeros((2, ny, p.nx, p.k + 1))
+    delta = np.zeros((2, p.nys, p.nxs, p.k + 1))
     sigma = np.zeros((2, p.nfields))
     avg = np.zeros((2, p.nfields))
     pc = p.c()
@@ -306,11 +326,11 @@ def eval_cells(p: Problem, u: np.ndarray, mesh: int, xi, eta=None) -> np.ndarray
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     eta = np.zeros_like(xi) if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
-    ny = p.ny if p.dim == 2 else 1
-    out = np.zeros((ny, p.nx, len(xi), p.nfields))
+    out = np.zeros((p.nys, p.nxs, len(xi), p.nfields))
     pc = p.c()
     lib().orc_eval_cells(ctypes.byref(pc), _dp(u), mesh, len(xi), _dp(xi), _dp(eta), _dp(out))
-    return out
+    ny = p.ny if p.dim == 2 else 1
+    return out if mesh == 1 else out[:ny, :p.nx]
 
 
 def eval_points(p: Problem, u: np.ndarray, mesh: int, xy: np.ndarray) -> np.ndarray:
