@@ -14,7 +14,7 @@
  *     the 1D Euler equations;
  *   - time stepping: forward Euler, SSP-RK2, SSP-RK3 or the classical
  *     four-stage RK4 (written in Shu-Osher form, used for Table 2);
- * all with periodic or transmissive boundaries.
+ * with periodic, transmissive or (Euler) reflective boundaries, set per side.
  *
  * Conventions shared by every entry point
  *   - Every call returns a cdg_status; nothing throws, aborts or exits.
@@ -29,7 +29,12 @@
  *     unnormalised Legendre polynomials P_a(xi) P_b(eta): Q^k at index
  *     b*(k+1) + a, P^k ordered by total degree a+b and then by decreasing a
  *     ((0,0), (1,0), (0,1), (2,0), (1,1), (0,2), ...); 1D: a = 0..k.  j is
- *     absent (ny = 1) in 1D.
+ *     absent (ny = 1) in 1D.  Both meshes' planes have nxs x nys cells: nx x ny,
+ *     plus one column (row) where the low x (y) side is a reflective wall.  The
+ *     dual mesh keeps its cell centred on that wall in the extra slot (i = nx,
+ *     resp. j = ny); the primal mesh leaves the slot unused (it is neither read
+ *     nor written; cdg_project_ic sets it to 0).  The dual cell centred on a
+ *     high-side wall is its ordinary last cell.
  *   - All calls are asynchronous on the context's stream unless stated.
  *   - tau and tau_max live in device memory owned by the context, so that a
  *     sequence of cdg_step_async calls can be captured in a CUDA graph.
@@ -57,7 +62,7 @@ typedef enum {
 
 enum { CDG_ADVECTION = 0, CDG_BURGERS = 1, CDG_EULER = 2 };
 enum { CDG_BASIS_Q = 0, CDG_BASIS_P = 1 };
-enum { CDG_PERIODIC = 0, CDG_TRANSMISSIVE = 1 };
+enum { CDG_PERIODIC = 0, CDG_TRANSMISSIVE = 1, CDG_REFLECTIVE = 2 };
 enum { CDG_RK_EULER1 = 1, CDG_RK_SSP2 = 2, CDG_RK_SSP3 = 3, CDG_RK_RK4 = 4 };
 
 /* Problem description (Section 2.1 meshes and spaces; Section 4 time stepping). */
@@ -67,10 +72,16 @@ typedef struct {
   int k;         /* polynomial degree: 1..3 */
   int basis;     /* CDG_BASIS_Q or CDG_BASIS_P (1D: P^k = Q^k, either accepted) */
   int system;    /* CDG_ADVECTION, CDG_BURGERS or CDG_EULER */
-  int bc;        /* CDG_PERIODIC or CDG_TRANSMISSIVE on every side */
+  int bc[4];     /* boundary condition of each side: x-low, x-high, y-low, y-high
+                    (1D: the first two).  CDG_PERIODIC (on both sides of a
+                    direction or on neither), CDG_TRANSMISSIVE (outflow: the
+                    ghost cell is a copy of the nearest cell), CDG_REFLECTIVE
+                    (a wall, Euler only: the restriction of the mirror-extended
+                    problem -- the state beyond the wall is the mirror image
+                    with the normal momentum negated; sigma and avg are those
+                    of the mirror-extended domain) */
   int oe;        /* 1: apply the OE step F_tau after every RK stage */
   int rk;        /* CDG_RK_EULER1, _SSP2, _SSP3 or _RK4 */
-  int pad;
   double ax, bx, ay, by; /* domain [ax,bx] x [ay,by] */
   double gamma;          /* ratio of specific heats (Euler) */
   double adv_x, adv_y;   /* advection velocity */
@@ -82,8 +93,13 @@ typedef struct cdg_ctx cdg_ctx;
 /* Create a context for the mesh pair of Section 2.1 (primal + dual), bound to
  * `stream` (a cudaStream_t; NULL = the legacy default stream), on the current
  * device.  Allocates the geometry constants and the scratch buffers.
- * Errors: CDG_EINVAL (null pointers, sizes < 2, bad enums), CDG_EUNSUPPORTED
- * (k outside 1..3), CDG_ENOMEM, CDG_ECUDA.  On error *out is NULL. */
+ * Contexts whose four sides are all periodic or all transmissive run the Q^2
+ * configurations on the tiled kernels; any other combination (and every
+ * reflective wall) runs on the degree-generic kernels.
+ * Errors: CDG_EINVAL (null pointers, sizes < 2, bad enums, a periodic side
+ * without its periodic partner, a reflective wall for a system other than
+ * Euler), CDG_EUNSUPPORTED (k outside 1..3), CDG_ENOMEM, CDG_ECUDA.  On error
+ * *out is NULL. */
 cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out);
 
 /* Release a context (synchronises its stream first).  NULL is accepted. */
@@ -92,14 +108,19 @@ cdg_status cdg_free(cdg_ctx* ctx);
 /* Static text describing the last error of `ctx` ("" if none; NULL ctx ok). */
 const char* cdg_last_error(const cdg_ctx* ctx);
 
-/* Number of FP64 elements of a state array (2 meshes x fields x modes x cells). */
+/* Number of FP64 elements of a state array (2 meshes x fields x modes x
+ * nxs x nys cells, the padded layout above). */
 cdg_status cdg_state_numel(const cdg_ctx* ctx, size_t* numel);
 
 /* Sampling points of the projection-based initialisation (Section 3.3): on
- * every cell of both meshes, (k+1) x (k+1) (1D: k + 1) Gauss points on each
- * of its 4 (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx] of (x, y) pairs (1D:
- * [mesh][i][sx][qx] of x).  With d_xy == NULL only *npts is set; otherwise
- * d_xy is a device array of npts * dim doubles. */
+ * every stored cell of both meshes (the padded layout; an unused primal slot
+ * gets valid points whose values are ignored), (k+1) x (k+1) (1D: k + 1) Gauss
+ * points on each of its 4 (1D: 2) sub-cells, layout [mesh][j][i][sy][sx][qy][qx]
+ * of (x, y) pairs (1D: [mesh][i][sx][qx] of x).  The outer half of a
+ * wall-centred dual cell lies beyond the wall: its points are folded back to
+ * their mirror images inside, and cdg_project_ic negates the normal momentum
+ * sampled there.  With d_xy == NULL only *npts is set; otherwise d_xy is a
+ * device array of npts * dim doubles. */
 cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts);
 
 /* L^2 projection of sampled initial data onto both meshes (the projection-
@@ -157,8 +178,8 @@ cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double*
  * A non-physical cell average sets the context's status flag. */
 cdg_status cdg_oe_damp(cdg_ctx* ctx, const double* d_uh, double* d_usig);
 
-/* The damping coefficients alone, for inspection: d_delta [2][ny][nx][k+1],
- * d_sigma [2][fields] (either may be NULL). */
+/* The damping coefficients alone, for inspection: d_delta [2][nys][nxs][k+1]
+ * (the padded layout), d_sigma [2][fields] (either may be NULL). */
 cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta, double* d_sigma);
 
 /* nsteps full time steps of Eq. (eq:RKCDG) in place on d_u, starting at time t

@@ -79,12 +79,18 @@ __device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restric
   double fL[F], fR[F];
 #pragma unroll
   for (int sx = 0; sx < 2; ++sx) {
-    const double* c = uo + wrap_index<BC>(i + sx + off, g.nx);
+    bool mir = false;
+    const int oi = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, unwrapped(g, 0, mesh, i) + sx + off, mir)
+                                    : wrap_index<BC>(i + sx + off, g.nx);
+    const double* c = uo + oi;
     double w[F][M];
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int a = 0; a < M; ++a) w[f][a] = ldv<LD>(c + (f * M + a) * P);
+      for (int a = 0; a < M; ++a) {
+        w[f][a] = ldv<LD>(c + (f * M + a) * P);
+        if (BC == BC_GENERAL && mir) w[f][a] = apply_sign(w[f][a], mirror_sign(true, false, SYS == SYS_EULER, f, a, 0));
+      }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       const double xo = xo1(N, sx, q), xsf = xs1(N, sx, q);
@@ -140,7 +146,7 @@ __device__ __forceinline__ void stage_cell1d(const Geo& g, const double* __restr
                                              double* __restrict__ out, const double* __restrict__ dt,
                                              double* __restrict__ pblk, int mesh, int i) {
   constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
-  const bool active = i < g.nx;
+  const bool active = i < cells_x(g, mesh);
   const int ic = active ? i : 0;
   const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
   const double inv_tm = 1.0 / tm;
@@ -181,6 +187,7 @@ __device__ __forceinline__ void stage_cell1d(const Geo& g, const double* __restr
         mn = fmin(mn, val);
       }
       double s = active ? v[0] : 0.0;
+      if (BC == BC_GENERAL) s *= cell_weight(g, mesh, ic, 0, 1);  // a wall-centred dual cell counts half
       if (!active) {
         mx = -DINF1;
         mn = DINF1;
@@ -215,12 +222,15 @@ __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i) {
   constexpr int F = Fields1<SYS>::F, M = K + 1;
-  if (i >= g.nx) return;
+  if (i >= cells_x(g, mesh)) return;
   const long long P = g.plane;
   const double* us = uh + (long long)mesh * F * M * P + i;
   const double* uo = uh + (long long)(1 - mesh) * F * M * P;
   const int off = mesh == 0 ? -1 : 0;
-  const int oL = wrap_index<BC>(i + off, g.nx), oR = wrap_index<BC>(i + 1 + off, g.nx);
+  bool mL = false, mR = false;
+  const int iu = BC == BC_GENERAL ? unwrapped(g, 0, mesh, i) : i;
+  const int oL = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, iu + off, mL) : wrap_index<BC>(i + off, g.nx);
+  const int oR = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, iu + 1 + off, mR) : wrap_index<BC>(i + 1 + off, g.nx);
   double wa[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) wa[f] = ldv<LD>(us + (f * M) * P);
@@ -252,6 +262,10 @@ __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict
       u[a] = ldv<LD>(us + (f * M + a) * P);
       l[a] = ldv<LD>(uo + (f * M + a) * P + oL);
       r[a] = ldv<LD>(uo + (f * M + a) * P + oR);
+      if (BC == BC_GENERAL) {  // mirror images beyond a wall
+        l[a] = apply_sign(l[a], mirror_sign(mL, false, SYS == SYS_EULER, f, a, 0));
+        r[a] = apply_sign(r[a], mirror_sign(mR, false, SYS == SYS_EULER, f, a, 0));
+      }
     }
     if (sg != 0.0) {
       const double is = beta / sg;
@@ -272,7 +286,7 @@ __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict
     }
   }
   if (WRITE_DELTA) {
-    double* dp = delta_out + ((long long)mesh * g.nx + i) * M;
+    double* dp = delta_out + ((long long)mesh * g.nxs + i) * M;
 #pragma unroll
     for (int m = 0; m < M; ++m) dp[m] = dl[m];
   }
@@ -312,6 +326,7 @@ __global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
+    if (cell >= cells_x(g, mesh)) continue;  // the primal mesh's unused slot
     const double* us = u + (long long)mesh * F * M * g.plane + cell;
     double w[F];
 #pragma unroll
@@ -330,7 +345,7 @@ __global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict
 // Sampling points of the initial projection: K+1 Gauss points on each half of
 // every cell of both meshes, layout [mesh][i][s][q].
 template <int K>
-__global__ void k_points1d(Geo g, double ax, double* __restrict__ x) {
+__global__ void k_points1d(Geo g, double ax, double bx, double* __restrict__ x) {
   constexpr int N = K + 1, R = 2 * N;
   const long long n = 2 * g.plane * R;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -338,8 +353,13 @@ __global__ void k_points1d(Geo g, double ax, double* __restrict__ x) {
     const long long c = t / R;
     const int mesh = (int)(c / g.plane);
     const long long i = c - mesh * g.plane;
-    const double xc = ax + (i + 0.5 + 0.5 * mesh) * g.hx;
-    x[t] = xc + 0.5 * g.hx * xs1(N, r / N, r % N);
+    // the unused primal slot takes the dual cell's points (ignored)
+    const int cm = i < cells_x(g, mesh) ? mesh : 1;
+    const double xc = ax + (unwrapped(g, 0, cm, (int)i) + 0.5 + 0.5 * cm) * g.hx;
+    double xp = xc + 0.5 * g.hx * xs1(N, r / N, r % N);
+    if (g.bcs[0] == SIDE_REFLECTIVE && xp < ax) xp = 2.0 * ax - xp;  // folded back across a wall
+    if (g.bcs[1] == SIDE_REFLECTIVE && xp > bx) xp = 2.0 * bx - xp;
+    x[t] = xp;
   }
 }
 
@@ -358,21 +378,27 @@ __global__ void k_project1d(Geo g, const double* __restrict__ vals, double* __re
 #pragma unroll
       for (int a = 0; a < M; ++a) acc[f][a] = 0.0;
     const double* v = vals + c * R * F;
+    // the outer half of a wall-centred dual cell was sampled at its mirror
+    // image inside: the normal momentum (Euler, field 1) changes sign there
+    const bool wl = mesh == 1 && g.bcs[0] == SIDE_REFLECTIVE && cell == g.nx;
+    const bool wr = mesh == 1 && g.bcs[1] == SIDE_REFLECTIVE && cell == g.nx - 1;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const double xi = xs1(N, r / N, r % N), w = 0.5 * gw1(N, r % N);
+      const bool folded = (wl && r / N == 0) || (wr && r / N == 1);
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        const double x = w * v[r * F + f];
+        const double x = (folded && F == 3 && f == 1) ? -w * v[r * F + f] : w * v[r * F + f];
 #pragma unroll
         for (int a = 0; a < M; ++a) acc[f][a] = fma(x, lpd(a, 0, xi), acc[f][a]);
       }
     }
+    const bool used = cell < cells_x(g, mesh);  // the primal mesh's unused slot is set to 0
     double* o = u + (long long)mesh * F * M * g.plane + cell;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int a = 0; a < M; ++a) o[(f * M + a) * g.plane] = acc[f][a] * ((2 * a + 1) / 2.0);
+      for (int a = 0; a < M; ++a) o[(f * M + a) * g.plane] = used ? acc[f][a] * ((2 * a + 1) / 2.0) : 0.0;
   }
 }
 
@@ -390,6 +416,7 @@ __device__ __forceinline__ void persist_wave1d(const Geo& g, const Persist1& a, 
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     const int mesh = (int)(c / g.plane);
+    if (c - mesh * g.plane >= cells_x(g, mesh)) continue;  // the primal mesh's unused slot
     const double* uc = u + (long long)mesh * F * M * g.plane + (c - mesh * g.plane);
     double w[F];
 #pragma unroll
@@ -437,7 +464,7 @@ __global__ void __launch_bounds__(NT1) k_persist1d(Geo g, Persist1 a) {
       }
       if (a.oe && last_block(a.bar + 1)) {
         for (int it = threadIdx.x >> 5; it < 2 * F; it += blockDim.x >> 5)
-          warp_sigma<LD_CA>(a.partials, a.nblk, F, it / F, it % F, g.plane, a.avg, a.sigma);
+          warp_sigma<LD_CA>(a.partials, a.nblk, F, it / F, it % F, a.sn, a.avg, a.sigma);
       }
       if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
       if (a.oe) {
@@ -473,18 +500,19 @@ static void by_sys_bc_k(int sys, int bc, int k, Fn&& fn) {
   };
   auto bb = [&](auto S) {
     if (bc == BC_PERIODIC) kk(S, IC<BC_PERIODIC>{});
-    else kk(S, IC<BC_TRANSMISSIVE>{});
+    else if (bc == BC_TRANSMISSIVE) kk(S, IC<BC_TRANSMISSIVE>{});
+    else kk(S, IC<BC_GENERAL>{});
   };
   if (sys == SYS_EULER) bb(IC<SYS_EULER>{});
   else if (sys == SYS_BURGERS) bb(IC<SYS_BURGERS>{});
   else bb(IC<SYS_ADV>{});
 }
 
-long long partial_blocks_1d(const Geo& g) { return (g.nx + NT1 - 1) / NT1; }
+long long partial_blocks_1d(const Geo& g) { return (g.nxs + NT1 - 1) / NT1; }
 
 cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, const double* uin,
                            const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st) {
-  const dim3 grid((g.nx + NT1 - 1) / NT1, 2);
+  const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);
   by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
     constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
     if (rhs_only) k_stage1d<S_, B_, K_, MODE1_RHS><<<grid, NT1, 0, st>>>(g, uin, cb, out, dt, partials);
@@ -495,7 +523,7 @@ cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, c
 
 cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
                         const double* sigma, double* delta, int* status, cudaStream_t st) {
-  const dim3 grid((g.nx + NT1 - 1) / NT1, 2);
+  const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);
   by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
     constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
     if (delta) k_oe1d<S_, B_, K_, true><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
@@ -562,10 +590,10 @@ cudaError_t launch_persist1d(int sys, int bc, int k, const Geo& g, const Persist
   return e;
 }
 
-cudaError_t launch_points1d(int k, const Geo& g, double ax, double* x, cudaStream_t st) {
-  if (k == 1) k_points1d<1><<<256, 256, 0, st>>>(g, ax, x);
-  else if (k == 2) k_points1d<2><<<256, 256, 0, st>>>(g, ax, x);
-  else k_points1d<3><<<256, 256, 0, st>>>(g, ax, x);
+cudaError_t launch_points1d(int k, const Geo& g, double ax, double bx, double* x, cudaStream_t st) {
+  if (k == 1) k_points1d<1><<<256, 256, 0, st>>>(g, ax, bx, x);
+  else if (k == 2) k_points1d<2><<<256, 256, 0, st>>>(g, ax, bx, x);
+  else k_points1d<3><<<256, 256, 0, st>>>(g, ax, bx, x);
   return cudaGetLastError();
 }
 

@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(NT, OECDG_STAGE_MINB) k_stage2d(Geo g, const d
 // field (Section 2.2): avg = mean of the cell averages over the stored cells,
 // sigma = max(max - avg, avg - min) over the cell Gauss points.  grid = (F, 2),
 // one warp each: the same code as the persistent kernels' sigma phase.
-__global__ void k_sigma(const double* __restrict__ partials, long long nblk, int F, long long ncell,
+__global__ void k_sigma(const double* __restrict__ partials, long long nblk, int F, SigmaNorm sn,
                         double* __restrict__ sigma, double* __restrict__ avg) {
-  warp_sigma<LD_NC>(partials, nblk, F, blockIdx.y, blockIdx.x, ncell, avg, sigma);
+  warp_sigma<LD_NC>(partials, nblk, F, blockIdx.y, blockIdx.x, sn, avg, sigma);
 }
 
 // ---------------------------------------------------------------- OE step --
@@ -205,9 +205,9 @@ cudaError_t launch_stage2d(int sys, int bc, const Geo& g, int rhs_only, const do
                            : stage2d_t<SYS_ADV, BC_TRANSMISSIVE>(g, mode, uin, un, out, dt, ca, cb, partials, st);
 }
 
-cudaError_t launch_sigma(const double* partials, long long nblk, int F, long long ncell, double* sigma, double* avg,
-                         cudaStream_t st) {
-  k_sigma<<<dim3(F, 2), 32, 0, st>>>(partials, nblk, F, ncell, sigma, avg);
+cudaError_t launch_sigma(const double* partials, long long nblk, int F, const SigmaNorm& sn, double* sigma,
+                         double* avg, cudaStream_t st) {
+  k_sigma<<<dim3(F, 2), 32, 0, st>>>(partials, nblk, F, sn, sigma, avg);
   return cudaGetLastError();
 }
 

@@ -135,6 +135,7 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
   const double* uo = u + (long long)(1 - mesh) * F * M * P;
   const int off = mesh == 0 ? -1 : 0;
   const double sx2 = 2.0 / g.hx, sy2 = 2.0 / g.hy;
+  const int iu = BC == BC_GENERAL ? unwrapped(g, 0, mesh, i) : i, ju = BC == BC_GENERAL ? unwrapped(g, 1, mesh, j) : j;
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -142,8 +143,10 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
 #pragma unroll 1
   for (int sub = 0; sub < 4; ++sub) {
     const int sx = sub & 1, sy = sub >> 1;
-    const int oi = wrap_index<BC>(i + sx + off, g.nx), oj = wrap_index<BC>(j + sy + off, g.ny);
-    const double* c = uo + (long long)oj * g.nx + oi;
+    bool mx = false, my = false;  // the overlapping cell is a mirror image across a wall
+    const int oi = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, iu + sx + off, mx) : wrap_index<BC>(i + sx + off, g.nx);
+    const int oj = BC == BC_GENERAL ? side_index(g, 1, 1 - mesh, ju + sy + off, my) : wrap_index<BC>(j + sy + off, g.ny);
+    const double* c = uo + (long long)oj * g.nxs + oi;
     // ---- volume and dissipation terms on sub-cell (sx, sy), row by row
 #pragma unroll 1
     for (int qy = 0; qy < N; ++qy) {
@@ -157,8 +160,11 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
 #pragma unroll
           for (int a = 0; a <= K; ++a) T[f][a] = 0.0;
 #pragma unroll
-          for (int m = 0; m < M; ++m)
-            T[f][MD::a(m)] = fma(pyo[MD::b(m)], __ldg(c + (f * M + m) * P), T[f][MD::a(m)]);
+          for (int m = 0; m < M; ++m) {
+            double cv = __ldg(c + (f * M + m) * P);
+            if (BC == BC_GENERAL) cv = apply_sign(cv, mirror_sign(mx, my, SYS == SYS_EULER, f, MD::a(m), MD::b(m)));
+            T[f][MD::a(m)] = fma(pyo[MD::b(m)], cv, T[f][MD::a(m)]);
+          }
         }
       }
       double X[F][K + 1], Y[F][K + 1];
@@ -222,7 +228,9 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             const int an = dir == 0 ? MD::a(m) : MD::b(m), at = dir == 0 ? MD::b(m) : MD::a(m);
-            Z[f][at] = fma(p0[an], __ldg(c + (f * M + m) * P), Z[f][at]);
+            double cv = __ldg(c + (f * M + m) * P);
+            if (BC == BC_GENERAL) cv = apply_sign(cv, mirror_sign(mx, my, SYS == SYS_EULER, f, MD::a(m), MD::b(m)));
+            Z[f][at] = fma(p0[an], cv, Z[f][at]);
           }
         }
       }
@@ -265,7 +273,7 @@ __device__ __forceinline__ void cell_rhs2k(const Geo& g, const double* __restric
         }
     }
   }
-  const double* us = u + (long long)mesh * F * M * P + (long long)j * g.nx + i;
+  const double* us = u + (long long)mesh * F * M * P + (long long)j * g.nxs + i;
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -295,13 +303,13 @@ __global__ void __launch_bounds__(NTK) k_stage2k(Geo g, const double* __restrict
   const int mesh = blockIdx.z;
   int i, j;
   cell_of_thread(g, i, j);
-  const bool active = i < g.nx && j < g.ny;
+  const bool active = i < cells_x(g, mesh) && j < cells_y(g, mesh);
   const int ic = active ? i : 0, jc = active ? j : 0;
   const double tau = dt[0], tm = dt[1];
   double L[F][M];
   cell_rhs2k<SYS, BC, K, B>(g, uin, mesh, ic, jc, 1.0 / tm, L);
   const long long P = g.plane;
-  const long long base = (long long)mesh * F * M * P + (long long)jc * g.nx + ic;
+  const long long base = (long long)mesh * F * M * P + (long long)jc * g.nxs + ic;
   if (MODE == MODEK_RHS) {
     if (active)
 #pragma unroll
@@ -338,6 +346,7 @@ __global__ void __launch_bounds__(NTK) k_stage2k(Geo g, const double* __restrict
         mn = fmin(mn, val);
       }
       double s = active ? v[0] : 0.0;
+      if (BC == BC_GENERAL) s *= cell_weight(g, mesh, ic, jc, 2);  // wall-centred dual cells count half
       if (!active) {
         mx = -DINFK;
         mn = DINFK;
@@ -372,11 +381,12 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
   const int mesh = blockIdx.z;
   int i, j;
   cell_of_thread(g, i, j);
-  if (i >= g.nx || j >= g.ny) return;
+  if (i >= cells_x(g, mesh) || j >= cells_y(g, mesh)) return;
   const long long P = g.plane;
-  const double* us = uh + (long long)mesh * F * M * P + (long long)j * g.nx + i;
+  const double* us = uh + (long long)mesh * F * M * P + (long long)j * g.nxs + i;
   const double* uo = uh + (long long)(1 - mesh) * F * M * P;
   const int off = mesh == 0 ? -1 : 0;
+  const int iu = BC == BC_GENERAL ? unwrapped(g, 0, mesh, i) : i, ju = BC == BC_GENERAL ? unwrapped(g, 1, mesh, j) : j;
   double wa[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) wa[f] = __ldg(us + (f * M) * P);
@@ -424,9 +434,12 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
         }
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          const int oi = wrap_index<BC>(i + (n == 0 ? side : h) + off, g.nx);
-          const int oj = wrap_index<BC>(j + (n == 0 ? h : side) + off, g.ny);
-          const double* co = uo + (long long)(f * M) * P + (long long)oj * g.nx + oi;
+          bool mx = false, my = false;  // a mirror image across a wall
+          const int oi = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, iu + (n == 0 ? side : h) + off, mx)
+                                          : wrap_index<BC>(i + (n == 0 ? side : h) + off, g.nx);
+          const int oj = BC == BC_GENERAL ? side_index(g, 1, 1 - mesh, ju + (n == 0 ? h : side) + off, my)
+                                          : wrap_index<BC>(j + (n == 0 ? h : side) + off, g.ny);
+          const double* co = uo + (long long)(f * M) * P + (long long)oj * g.nxs + oi;
           // the overlapping cell's series on its centre line (normal coordinate 0)
           double Tw[K + 1][K + 1];
 #pragma unroll
@@ -436,7 +449,8 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
 #pragma unroll
           for (int mm = 0; mm < M; ++mm) {
             const int a_n = n == 0 ? MD::a(mm) : MD::b(mm), a_t = n == 0 ? MD::b(mm) : MD::a(mm);
-            const double cw = __ldg(co + (long long)mm * P);
+            double cw = __ldg(co + (long long)mm * P);
+            if (BC == BC_GENERAL) cw = apply_sign(cw, mirror_sign(mx, my, SYS == SYS_EULER, f, MD::a(mm), MD::b(mm)));
 #pragma unroll
             for (int d = 0; d <= a_n; ++d)
               if (lpd(a_n, d, 0.0) != 0.0) Tw[d][a_t] = fma(lpd(a_n, d, 0.0), cw, Tw[d][a_t]);
@@ -498,7 +512,7 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
     }
   }
   if (WRITE_DELTA) {
-    double* dp = delta_out + (((long long)mesh * g.ny + j) * g.nx + i) * (K + 1);
+    double* dp = delta_out + (((long long)mesh * g.nys + j) * g.nxs + i) * (K + 1);
 #pragma unroll
     for (int m = 0; m <= K; ++m) dp[m] = dl[m];
   }
@@ -516,7 +530,7 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
         e[d] = e[K];
       }
     }
-    double* os = usig + (long long)mesh * F * M * P + (long long)j * g.nx + i;
+    double* os = usig + (long long)mesh * F * M * P + (long long)j * g.nxs + i;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -538,6 +552,8 @@ __global__ void k_wave2k(Geo g, const double* __restrict__ u, double* __restrict
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
+    const int cj = (int)(cell / g.nxs), ci = (int)(cell - (long long)cj * g.nxs);
+    if (ci >= cells_x(g, mesh) || cj >= cells_y(g, mesh)) continue;  // the primal mesh's unused slots
     const double* us = u + (long long)mesh * F * M * g.plane + cell;
     double w[F];
 #pragma unroll
@@ -560,10 +576,13 @@ __global__ void k_wave2k(Geo g, const double* __restrict__ u, double* __restrict
 }
 
 // Sampling points of the initial projection: (k+1)^2 Gauss points on each of
-// the 4 sub-cells of every cell of both meshes, layout
-// [mesh][j][i][sy][sx][qy][qx] of (x, y).
+// the 4 sub-cells of every stored cell of both meshes (the padded layout: an
+// unused primal slot takes the dual cell's points), layout
+// [mesh][j][i][sy][sx][qy][qx] of (x, y); points beyond a reflective wall
+// (the outer half of a wall-centred dual cell) folded back to their mirror
+// images inside [ax, bx] x [ay, by].
 template <int K>
-__global__ void k_points2k(Geo g, double ax, double ay, double* __restrict__ xy) {
+__global__ void k_points2k(Geo g, double ax, double ay, double bx, double by, double* __restrict__ xy) {
   constexpr int N = K + 1, R = 4 * N * N;
   const long long n = 2 * g.plane * R;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -571,11 +590,18 @@ __global__ void k_points2k(Geo g, double ax, double ay, double* __restrict__ xy)
     const long long c = t / R;
     const int mesh = (int)(c / g.plane);
     const long long cell = c - mesh * g.plane;
-    const int j = (int)(cell / g.nx), i = (int)(cell - (long long)j * g.nx);
+    const int j = (int)(cell / g.nxs), i = (int)(cell - (long long)j * g.nxs);
+    const int cm = (i < cells_x(g, mesh) && j < cells_y(g, mesh)) ? mesh : 1;
     const int qx = r % N, qy = (r / N) % N, sx = (r / (N * N)) % 2, sy = r / (2 * N * N);
-    const double xc = ax + (i + 0.5 + 0.5 * mesh) * g.hx, yc = ay + (j + 0.5 + 0.5 * mesh) * g.hy;
-    xy[2 * t] = xc + 0.5 * g.hx * xs1(N, sx, qx);
-    xy[2 * t + 1] = yc + 0.5 * g.hy * xs1(N, sy, qy);
+    const double xc = ax + (unwrapped(g, 0, cm, i) + 0.5 + 0.5 * cm) * g.hx;
+    const double yc = ay + (unwrapped(g, 1, cm, j) + 0.5 + 0.5 * cm) * g.hy;
+    double x = xc + 0.5 * g.hx * xs1(N, sx, qx), y = yc + 0.5 * g.hy * xs1(N, sy, qy);
+    if (g.bcs[0] == SIDE_REFLECTIVE && x < ax) x = 2.0 * ax - x;
+    if (g.bcs[1] == SIDE_REFLECTIVE && x > bx) x = 2.0 * bx - x;
+    if (g.bcs[2] == SIDE_REFLECTIVE && y < ay) y = 2.0 * ay - y;
+    if (g.bcs[3] == SIDE_REFLECTIVE && y > by) y = 2.0 * by - y;
+    xy[2 * t] = x;
+    xy[2 * t + 1] = y;
   }
 }
 
@@ -595,6 +621,13 @@ __global__ void k_project2k(Geo g, const double* __restrict__ vals, double* __re
 #pragma unroll
       for (int m = 0; m < M; ++m) acc[f][m] = 0.0;
     const double* v = vals + c * R * F;
+    const int cj = (int)(cell / g.nxs), ci = (int)(cell - (long long)cj * g.nxs);
+    // sub-cells beyond a wall were sampled at their mirror images: the normal
+    // momentum (Euler: field 1 for x, 2 for y) changes sign there
+    const bool wxl = mesh == 1 && g.bcs[0] == SIDE_REFLECTIVE && ci == g.nx;
+    const bool wxh = mesh == 1 && g.bcs[1] == SIDE_REFLECTIVE && ci == g.nx - 1;
+    const bool wyl = mesh == 1 && g.bcs[2] == SIDE_REFLECTIVE && cj == g.ny;
+    const bool wyh = mesh == 1 && g.bcs[3] == SIDE_REFLECTIVE && cj == g.ny - 1;
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
       const int qx = r % N, qy = (r / N) % N, sx = (r / (N * N)) % 2, sy = r / (2 * N * N);
@@ -602,19 +635,23 @@ __global__ void k_project2k(Geo g, const double* __restrict__ vals, double* __re
       leg_row<K, 0>(sx - 0.5 + 0.5 * GNK[N - 2][qx], px);
       leg_row<K, 0>(sy - 0.5 + 0.5 * GNK[N - 2][qy], py);
       const double w = 0.25 * GWK[N - 2][qx] * GWK[N - 2][qy];
+      const bool fx = (wxl && sx == 0) || (wxh && sx == 1), fy = (wyl && sy == 0) || (wyh && sy == 1);
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        const double x = w * v[r * F + f];
+        const bool neg = F == 4 && ((fx && f == 1) || (fy && f == 2));
+        const double x = neg ? -w * v[r * F + f] : w * v[r * F + f];
 #pragma unroll
         for (int m = 0; m < M; ++m) acc[f][m] = fma(x, px[MD::a(m)] * py[MD::b(m)], acc[f][m]);
       }
     }
+    const bool used = ci < cells_x(g, mesh) && cj < cells_y(g, mesh);  // unused primal slots: 0
     double* o = u + (long long)mesh * F * M * g.plane + cell;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
       for (int m = 0; m < M; ++m)
-        o[(long long)(f * M + m) * g.plane] = acc[f][m] * ((2 * MD::a(m) + 1) * (2 * MD::b(m) + 1) / 4.0);
+        o[(long long)(f * M + m) * g.plane] =
+            used ? acc[f][m] * ((2 * MD::a(m) + 1) * (2 * MD::b(m) + 1) / 4.0) : 0.0;
   }
 }
 
@@ -639,14 +676,15 @@ static void by_sys_bc_k_b(int sys, int bc, int k, int basis, Fn&& fn) {
   };
   auto bb = [&](auto S) {
     if (bc == BC_PERIODIC) kb(S, ICk<BC_PERIODIC>{});
-    else kb(S, ICk<BC_TRANSMISSIVE>{});
+    else if (bc == BC_TRANSMISSIVE) kb(S, ICk<BC_TRANSMISSIVE>{});
+    else kb(S, ICk<BC_GENERAL>{});
   };
   if (sys == SYS_EULER) bb(ICk<SYS_EULER>{});
   else if (sys == SYS_BURGERS) bb(ICk<SYS_BURGERS>{});
   else bb(ICk<SYS_ADV>{});
 }
 
-static dim3 grid2k(const Geo& g) { return dim3((g.nx + 31) / 32, (g.ny + NTK / 32 - 1) / (NTK / 32), 2); }
+static dim3 grid2k(const Geo& g) { return dim3((g.nxs + 31) / 32, (g.nys + NTK / 32 - 1) / (NTK / 32), 2); }
 
 long long partial_blocks_2k(const Geo& g) {
   const dim3 gr = grid2k(g);
@@ -688,10 +726,11 @@ cudaError_t launch_dt2k(int sys, int k, int basis, const Geo& g, const double* u
   return launch_dt_final(partial, nblk, g.hx, g.hy, 2, g.cfl, T_end, dt, time, st);
 }
 
-cudaError_t launch_points2k(int k, const Geo& g, double ax, double ay, double* xy, cudaStream_t st) {
-  if (k == 1) k_points2k<1><<<1184, 256, 0, st>>>(g, ax, ay, xy);
-  else if (k == 2) k_points2k<2><<<1184, 256, 0, st>>>(g, ax, ay, xy);
-  else k_points2k<3><<<1184, 256, 0, st>>>(g, ax, ay, xy);
+cudaError_t launch_points2k(int k, const Geo& g, double ax, double ay, double bx, double by, double* xy,
+                            cudaStream_t st) {
+  if (k == 1) k_points2k<1><<<1184, 256, 0, st>>>(g, ax, ay, bx, by, xy);
+  else if (k == 2) k_points2k<2><<<1184, 256, 0, st>>>(g, ax, ay, bx, by, xy);
+  else k_points2k<3><<<1184, 256, 0, st>>>(g, ax, ay, bx, by, xy);
   return cudaGetLastError();
 }
 

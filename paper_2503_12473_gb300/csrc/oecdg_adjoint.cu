@@ -1094,7 +1094,7 @@ static cudaError_t adj_forward(cdg_ctx* c, const double* un, double* const* H, d
     // (into the stage buffer H[2]'s partner slot) for its record
     double* dst = l < 2 ? S[l] : (u_next ? u_next : a->LI);
     if (oe) {
-      if ((e = launch_sigma(c->partials, c->nblk, F, g.plane, c->sigma, c->avg, st)) != cudaSuccess) return e;
+      if ((e = launch_sigma(c->partials, c->nblk, F, plain_norm(g.plane), c->sigma, c->avg, st)) != cudaSuccess) return e;
       const dim3 grid((g.nx + 31) / 32, (g.ny + AT / 32 - 1) / (AT / 32), 2);
       // the variant the forward step uses (square cells: isotropic), so the
       // recorded states equal cdg_step's
@@ -1149,7 +1149,7 @@ static cudaError_t adj_backward(cdg_ctx* c, const double* un, const double* cons
 }
 
 static cdg_status adj_check(cdg_ctx* ctx) {
-  if (ctx->d.dim != 2 || ctx->gen2 || ctx->d.bc != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
+  if (ctx->d.dim != 2 || ctx->gen2 || uniform_side_bc(ctx->d) != CDG_PERIODIC || ctx->d.rk != CDG_RK_SSP3)
     return adj_fail(ctx, CDG_EUNSUPPORTED, "adjoint: 2D periodic Q^2 SSP-RK3 only");
   cdg_status s = adj_alloc(ctx);
   if (s != CDG_OK) return adj_fail(ctx, s, "adjoint: allocation failed");

@@ -63,7 +63,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   const cdg_mesh_desc& d = *desc;
   if (d.dim != 1 && d.dim != 2) return CDG_EINVAL;
   if (d.nx < 2 || (d.dim == 2 && d.ny < 2)) return CDG_EINVAL;
-  if (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE) return CDG_EINVAL;
+  if (invalid_sides(d)) return CDG_EINVAL;
   if (d.system != CDG_ADVECTION && d.system != CDG_BURGERS && d.system != CDG_EULER) return CDG_EINVAL;
   if (d.rk < CDG_RK_EULER1 || d.rk > CDG_RK_RK4) return CDG_EINVAL;
   if (d.basis != CDG_BASIS_Q && d.basis != CDG_BASIS_P) return CDG_EINVAL;
@@ -80,15 +80,18 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   c->stream = (cudaStream_t)stream;
   c->F = d.system == CDG_EULER ? d.dim + 2 : 1;
   // the tiled kernels serve Q^2 with forward Euler / SSP-RK2 / SSP-RK3 for
-  // advection and Euler; every other 2D configuration runs the generic ones
-  c->gen2 = d.dim == 2 && (d.k != 2 || d.basis != CDG_BASIS_Q || d.system == CDG_BURGERS || d.rk == CDG_RK_RK4);
+  // advection and Euler with the same periodic or transmissive condition on
+  // every side; every other 2D configuration runs the generic ones
+  const int ubc = uniform_side_bc(d);
+  c->gen2 = d.dim == 2 &&
+            (d.k != 2 || d.basis != CDG_BASIS_Q || d.system == CDG_BURGERS || d.rk == CDG_RK_RK4 || ubc < 0);
   c->M = d.dim == 2 ? modes_2k(d.k, d.basis == CDG_BASIS_Q ? BASIS_Q : BASIS_P) : d.k + 1;
   c->sys = d.system == CDG_EULER ? SYS_EULER : d.system == CDG_BURGERS ? SYS_BURGERS : SYS_ADV;
-  c->bc = d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
+  c->bc = ubc < 0 ? BC_GENERAL : (ubc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE);
   Geo& g = c->g;
   g.nx = d.nx;
   g.ny = (int)ny;
-  g.plane = (long long)d.nx * ny;
+  geo_sides(d, g);
   g.hx = (d.bx - d.ax) / d.nx;
   g.hy = d.dim == 2 ? (d.by - d.ay) / d.ny : 1.0;
   g.gamma = d.gamma;
@@ -126,6 +129,13 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, 2 * sizeof(double), c->stream);
+  // the scratch states start at 0, so that the primal mesh's unused slots of
+  // the padded layout (walls) stay 0 through every stage and copy
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf_a, 0, c->numel * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf_b, 0, c->numel * sizeof(double), c->stream);
+  if (e == cudaSuccess && c->buf_c) e = cudaMemsetAsync(c->buf_c, 0, c->numel * sizeof(double), c->stream);
+  if (e == cudaSuccess && c->buf_d) e = cudaMemsetAsync(c->buf_d, 0, c->numel * sizeof(double), c->stream);
+  c->sn = sigma_norm(d, g);
   if (e != cudaSuccess) {
     cdg_free(c);
     return CDG_ECUDA;
@@ -180,11 +190,12 @@ cdg_status cdg_quad_points(cdg_ctx* ctx, double* d_xy, size_t* npts) {
   if (!ctx || !npts) return CDG_EINVAL;
   const size_t q = ctx->d.k + 1;
   const size_t per = ctx->d.dim == 2 ? 4 * q * q : 2 * q;
-  *npts = (size_t)2 * ctx->g.plane * per;
+  *npts = (size_t)2 * ctx->g.plane * per;  // the padded layout's cells
   if (!d_xy) return CDG_OK;
-  if (ctx->gen2) CK(launch_points2k(ctx->d.k, ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
+  if (ctx->gen2)
+    CK(launch_points2k(ctx->d.k, ctx->g, ctx->d.ax, ctx->d.ay, ctx->d.bx, ctx->d.by, d_xy, ctx->stream), "quad_points");
   else if (ctx->d.dim == 2) CK(launch_points2d(ctx->g, ctx->d.ax, ctx->d.ay, d_xy, ctx->stream), "quad_points");
-  else CK(launch_points1d(ctx->d.k, ctx->g, ctx->d.ax, d_xy, ctx->stream), "quad_points");
+  else CK(launch_points1d(ctx->d.k, ctx->g, ctx->d.ax, ctx->d.bx, d_xy, ctx->stream), "quad_points");
   ctx->launches += 1;
   return CDG_OK;
 }
@@ -250,7 +261,7 @@ static StageComb comb2(const double* u0, double c0, const double* u1, double c1,
 
 // sigma from the partials of the last stage kernel, then the OE kernel
 static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* delta) {
-  cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream);
+  cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->sn, ctx->sigma, ctx->avg, ctx->stream);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
   prof_mark(ctx, PROF_OE, 0);
@@ -404,7 +415,7 @@ cdg_status cdg_oe_coefficients(cdg_ctx* ctx, const double* d_uh, double* d_delta
      "oe_coefficients");
   if (d_delta) CK(run_oe(ctx, d_uh, nullptr, d_delta), "oe_coefficients");
   else {
-    CK(launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->g.plane, ctx->sigma, ctx->avg, ctx->stream),
+    CK(launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->sn, ctx->sigma, ctx->avg, ctx->stream),
        "oe_coefficients");
     ctx->launches += 1;
   }
@@ -556,6 +567,7 @@ cdg_status cdg_step_persistent(cdg_ctx* ctx, double* d_u, double t, double T_end
   a.nsteps = nsteps;
   a.T_end = T_end;
   a.nblk = ctx->nblk;
+  a.sn = ctx->sn;
   a.bar = ctx->p_bar;
   a.expected = (unsigned long long)ctx->p_grid + (unsigned long long)ctx->withhold;
   a.limit_ns = (unsigned long long)(ctx->wait_s * 1e9);

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
 // the fixed-order reduction shared with every other path
 __global__ void k_bsigma(const BatchInst* __restrict__ I, int F) {
   const BatchInst& in = I[blockIdx.z];
-  warp_sigma<LD_NC>(in.part, (long long)in.tx * in.ty, F, blockIdx.y, blockIdx.x, in.g.plane, in.avg, in.sigma);
+  warp_sigma<LD_NC>(in.part, (long long)in.tx * in.ty, F, blockIdx.y, blockIdx.x, plain_norm(in.g.plane), in.avg,
+                    in.sigma);
 }
 
 // per-instance maximum wave speeds over both meshes' cell averages: chunk ch
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
            it += (long long)gridDim.x * nw) {
         const BatchInst& in = a.I[it / (2 * F)];
         const int mesh = (int)((it / F) & 1), f = (int)(it % F);
-        warp_sigma<LD_CA>(in.part, (long long)in.tx * in.ty, F, mesh, f, in.g.plane, in.avg, in.sigma);
+        warp_sigma<LD_CA>(in.part, (long long)in.tx * in.ty, F, mesh, f, plain_norm(in.g.plane), in.avg, in.sigma);
       }
       if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
       for (long long b = blockIdx.x; b < a.ntiles; b += gridDim.x) {
@@ -430,7 +431,8 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
     if (d.dim != 2 || d.nx < 2 || d.ny < 2) return CDG_EINVAL;
     if (d.system != CDG_EULER || d.k != 2 || d.basis != CDG_BASIS_Q || d.rk != CDG_RK_SSP3 || d.oe != 1)
       return CDG_EUNSUPPORTED;
-    if (d.bc != descs[0].bc || (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE)) return CDG_EINVAL;
+    if (invalid_sides(d) || uniform_side_bc(d) < 0) return CDG_EINVAL;
+    if (uniform_side_bc(d) != uniform_side_bc(descs[0])) return CDG_EINVAL;
     if (!(d.bx > d.ax) || !(d.by > d.ay) || !(d.cfl > 0.0) || !(d.gamma > 1.0)) return CDG_EINVAL;
   }
   cdg_batch* B = (cdg_batch*)calloc(1, sizeof(cdg_batch));
@@ -438,7 +440,7 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
   B->n = n;
   B->F = 4;
   B->sys = SYS_EULER;
-  B->bc = descs[0].bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
+  B->bc = uniform_side_bc(descs[0]) == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
   B->h_inst = (BatchInst*)calloc(n, sizeof(BatchInst));
   B->h_ptrs = (double**)calloc(n, sizeof(double*));
   if (!B->h_inst || !B->h_ptrs) {
@@ -487,7 +489,7 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
     Geo& g = in.g;
     g.nx = d.nx;
     g.ny = d.ny;
-    g.plane = (long long)d.nx * d.ny;
+    geo_sides(d, g);  // uniform periodic or transmissive: no padding
     g.hx = (d.bx - d.ax) / d.nx;
     g.hy = (d.by - d.ay) / d.ny;
     g.gamma = d.gamma;

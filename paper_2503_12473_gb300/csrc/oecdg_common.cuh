@@ -9,7 +9,11 @@
 namespace oecdg {
 
 enum { SYS_ADV = 0, SYS_BURGERS = 1, SYS_EULER = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+// Boundary handling of a kernel: BC_PERIODIC / BC_TRANSMISSIVE on every side
+// (compile-time), or BC_GENERAL: each side's condition read from Geo::bcs at
+// run time (periodic in pairs, transmissive, or a reflective wall).
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_GENERAL = 2 };
+enum { SIDE_PERIODIC = 0, SIDE_TRANSMISSIVE = 1, SIDE_REFLECTIVE = 2 };
 enum { BASIS_Q = 0, BASIS_P = 1 };
 
 // status bits written by kernels
@@ -80,14 +84,81 @@ __device__ __forceinline__ double sqrt_pos(double x) {
 }
 
 // Geometry and physics constants passed by value to every kernel.
+//   nx, ny:   primal cells per direction;
+//   nxs, nys: stored cells per row / rows of BOTH meshes' planes (the padded
+//             layout): nx, ny, plus one where a reflective wall on the low side
+//             gives the dual mesh the cell centred on that wall (stored in the
+//             slot after its last cell; the primal mesh leaves the slot unused);
+//   plane:    nxs * nys;
+//   bcs:      per side (x-low, x-high, y-low, y-high): SIDE_PERIODIC,
+//             SIDE_TRANSMISSIVE or SIDE_REFLECTIVE (read by BC_GENERAL kernels).
 struct Geo {
   int nx, ny;
-  long long plane;   // nx * ny (cells of one mesh)
+  long long plane;
   double hx, hy;
   double gamma;
   double adv_x, adv_y;
   double cfl;
+  int nxs, nys;
+  int bcs[4];
 };
+
+// Stored cells of mesh `mesh` per direction (the dual mesh has the wall slots).
+__host__ __device__ __forceinline__ int cells_x(const Geo& g, int mesh) { return mesh == 0 ? g.nx : g.nxs; }
+__host__ __device__ __forceinline__ int cells_y(const Geo& g, int mesh) { return mesh == 0 ? g.ny : g.nys; }
+
+// Unwrapped index of cell i of mesh `mesh` in direction dir: primal cell iu
+// spans [iu h, (iu+1) h], dual cell iu is centred on vertex iu + 1; the dual
+// slot after the last cell holds the cell centred on vertex 0 (iu = -1).
+__host__ __device__ __forceinline__ int unwrapped(const Geo& g, int dir, int mesh, int i) {
+  return (mesh == 1 && i == (dir == 0 ? g.nx : g.ny)) ? -1 : i;
+}
+
+// Stored index of the cell of mesh `mesh` with unwrapped index iu in direction
+// dir, under the per-side conditions; *mirror = true for the mirror image of a
+// stored cell across a reflective wall (primal -1 - iu / 2n - 1 - iu, dual
+// vertex v -> -v / 2n - v).  Only one cell beyond a side is ever asked for.
+__device__ __forceinline__ int side_index(const Geo& g, int dir, int mesh, int iu, bool& mirror) {
+  const int n = dir == 0 ? g.nx : g.ny;
+  const int lo = g.bcs[2 * dir], hi = g.bcs[2 * dir + 1];
+  mirror = false;
+  if (iu >= 0 && iu < n) return iu;
+  if (lo == SIDE_PERIODIC) return iu < 0 ? iu + n : iu - n;
+  if (iu < 0) {
+    if (lo == SIDE_TRANSMISSIVE) return 0;
+    if (mesh == 1 && iu == -1) return n;  // the wall-centred dual cell
+    mirror = true;
+    iu = mesh == 0 ? -1 - iu : -iu - 2;
+  } else {
+    if (hi == SIDE_TRANSMISSIVE) return n - 1;
+    mirror = true;
+    iu = mesh == 0 ? 2 * n - 1 - iu : 2 * n - iu - 2;
+  }
+  return iu < 0 ? 0 : (iu >= n ? n - 1 : iu);
+}
+
+// Sign bit to apply to coefficient (field f, mode degrees (a, b)) of a mirror
+// image: the mirror across a wall normal to x negates the odd-in-x modes and
+// the x-momentum (Euler: field 1), likewise for y (field 2 in 2D).
+__device__ __forceinline__ unsigned long long mirror_sign(bool mx, bool my, bool euler, int f, int a, int b) {
+  const int neg = (mx ? ((a & 1) ^ (euler && f == 1)) : 0) ^ (my ? ((b & 1) ^ (euler && f == 2)) : 0);
+  return neg ? 0x8000000000000000ULL : 0ULL;
+}
+__device__ __forceinline__ double apply_sign(double v, unsigned long long sgn) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)sgn);
+}
+
+// Weight of a cell in the domain average (sigma, avg): halved for each
+// reflective wall a dual cell is centred on (the mirror-extended domain holds
+// it once, every other cell twice).
+__host__ __device__ __forceinline__ double cell_weight(const Geo& g, int mesh, int i, int j, int dim) {
+  if (mesh == 0) return 1.0;
+  double w = 1.0;
+  if ((g.bcs[0] == SIDE_REFLECTIVE && i == g.nx) || (g.bcs[1] == SIDE_REFLECTIVE && i == g.nx - 1)) w *= 0.5;
+  if (dim == 2 && ((g.bcs[2] == SIDE_REFLECTIVE && j == g.ny) || (g.bcs[3] == SIDE_REFLECTIVE && j == g.ny - 1)))
+    w *= 0.5;
+  return w;
+}
 
 // 2D Euler flux components at a conserved state (rho, mx, my, E).  Every
 // multiply-add is an explicit fma: the compiler's own contraction may differ

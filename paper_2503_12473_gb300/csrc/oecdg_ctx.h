@@ -4,6 +4,7 @@
 
 #include "../../include/oecdg.h"
 #include "oecdg_common.cuh"
+#include "oecdg_persist.cuh"
 
 using oecdg::Geo;
 
@@ -24,6 +25,7 @@ struct cdg_ctx {
   int sys;               // SYS_ADV / SYS_BURGERS / SYS_EULER
   int bc;                // BC_PERIODIC / BC_TRANSMISSIVE
   int gen2;              // 2D configuration served by the degree-generic kernels
+  oecdg::SigmaNorm sn;   // sigma normalisation (walls: weighted counts, odd fields)
   double* partials;      // [2][nblk][F][3]
   double* wave_partial;  // [wave_blk][2]
   double* dt;            // [tau, tau_max]

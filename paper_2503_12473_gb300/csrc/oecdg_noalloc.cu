@@ -108,7 +108,8 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
   const cdg_mesh_desc& d = *desc;
   if (d.dim != 1 && d.dim != 2) return CDG_EINVAL;
   if (d.nx < 2 || (d.dim == 2 && d.ny < 2)) return CDG_EINVAL;
-  if (d.bc != CDG_PERIODIC && d.bc != CDG_TRANSMISSIVE) return CDG_EINVAL;
+  if (invalid_sides(d)) return CDG_EINVAL;
+  if (uniform_side_bc(d) < 0) return CDG_EUNSUPPORTED;  // per-side conditions and walls: context path only
   if (d.system != CDG_ADVECTION && d.system != CDG_EULER) return d.system == CDG_BURGERS ? CDG_EUNSUPPORTED : CDG_EINVAL;
   if (d.k != 2 || (d.dim == 2 && d.basis != CDG_BASIS_Q)) return CDG_EUNSUPPORTED;
   if (!(d.bx > d.ax) || (d.dim == 2 && !(d.by > d.ay))) return CDG_EINVAL;
@@ -132,7 +133,7 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
   Geo g;
   g.nx = d.nx;
   g.ny = (int)ny;
-  g.plane = cells;
+  geo_sides(d, g);  // uniform periodic or transmissive: no padding, plane = cells
   g.hx = (d.bx - d.ax) / d.nx;
   g.hy = d.dim == 2 ? (d.by - d.ay) / d.ny : 1.0;
   g.gamma = d.gamma;
@@ -140,7 +141,7 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
   g.adv_y = d.adv_y;
   g.cfl = d.cfl;
   const int sys = d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
-  const int bc = d.bc == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
+  const int bc = uniform_side_bc(d) == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
 
   // everything a previous call left behind is rewritten or cleared here
   if (launch_set2(dt, tau, 1.0, st) != cudaSuccess) return CDG_ECUDA;
@@ -154,7 +155,7 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
     else k_sigma_partials_na<1, 1><<<grid, NA_BLOCK, 0, st>>>(g, d_uh, partials, nblk);
   }
   if (cudaGetLastError() != cudaSuccess) return CDG_ECUDA;
-  if (launch_sigma(partials, nblk, F, cells, sigma, avg, st) != cudaSuccess) return CDG_ECUDA;
+  if (launch_sigma(partials, nblk, F, plain_norm(cells), sigma, avg, st) != cudaSuccess) return CDG_ECUDA;
   cudaError_t e = d.dim == 2 ? launch_oe2d(sys, bc, g, d_uh, d_usig, dt, sigma, nullptr, status, st)
                              : launch_oe1d(sys, bc, 2, g, d_uh, d_usig, dt, sigma, nullptr, status, st);
   return e == cudaSuccess ? CDG_OK : CDG_ECUDA;

@@ -92,13 +92,23 @@ __device__ __forceinline__ bool last_block(unsigned long long* tickets) {
   return last != 0;
 }
 
+// Normalisation of the sigma reduction: the (weighted) cell count of each mesh
+// and the fields (bit f) whose domain average is 0 by mirror symmetry (the
+// normal momentum beside a reflective wall).  Without walls: ncell = the
+// cells of a mesh, odd = 0.
+struct SigmaNorm {
+  double ncell[2];
+  int odd;
+};
+
 // avg and sigma of one (mesh, field) from the block partials [2][nblk][F][3]
-// (sum of cell averages, max, min), by one full warp in a fixed order: lane l
-// folds partials l, l + 32, ...; then a shuffle tree.  avg = sum / ncell,
-// sigma = max(max - avg, avg - min) (Section 2.2, sigma_K).
+// (sum of weighted cell averages, max, min), by one full warp in a fixed
+// order: lane l folds partials l, l + 32, ...; then a shuffle tree.
+// avg = sum / ncell (0 for an odd field), sigma = max(max - avg, avg - min)
+// (Section 2.2, sigma_K).
 template <int LD>
 __device__ __forceinline__ void warp_sigma(const double* part, long long nblk, int F, int mesh, int f,
-                                           long long ncell, double* avg, double* sigma) {
+                                           const SigmaNorm& sn, double* avg, double* sigma) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   double s = 0.0, mx = -__builtin_huge_val(), mn = __builtin_huge_val();
@@ -115,10 +125,18 @@ __device__ __forceinline__ void warp_sigma(const double* part, long long nblk, i
     mn = fmin(mn, __shfl_down_sync(full, mn, o));
   }
   if (lane == 0) {
-    const double a = s / (double)ncell;
+    const double a = ((sn.odd >> f) & 1) ? 0.0 : s / sn.ncell[mesh];
     avg[mesh * F + f] = a;
     sigma[mesh * F + f] = fmax(mx - a, a - mn);
   }
+}
+
+// The plain normalisation: every cell of a mesh counts once, no odd field.
+__host__ __device__ __forceinline__ SigmaNorm plain_norm(long long ncell) {
+  SigmaNorm sn;
+  sn.ncell[0] = sn.ncell[1] = (double)ncell;
+  sn.odd = 0;
+  return sn;
 }
 
 // tau_max = C_CFL / (beta_x/h_x + beta_y/h_y) (1D: C_CFL h / beta) from the

@@ -18,7 +18,7 @@ from . import build as _build
 CDG_OK, CDG_EINVAL, CDG_ENOMEM, CDG_ECUDA, CDG_ENONPHYSICAL, CDG_ETIMEOUT, CDG_EUNSUPPORTED = range(7)
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
-PERIODIC, TRANSMISSIVE = 0, 1
+PERIODIC, TRANSMISSIVE, REFLECTIVE = 0, 1, 2
 RK_EULER1, RK_SSP2, RK_SSP3, RK_RK4 = 1, 2, 3, 4
 MATH_RCP, MATH_SQRT = 0, 1
 BATCH_GRAPH, BATCH_PERSISTENT = 1, 2
@@ -48,8 +48,8 @@ class CdgError(RuntimeError):
 class cdg_mesh_desc(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("k", ctypes.c_int),
-        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int), ("oe", ctypes.c_int),
-        ("rk", ctypes.c_int), ("pad", ctypes.c_int),
+        ("basis", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int * 4), ("oe", ctypes.c_int),
+        ("rk", ctypes.c_int),
         ("ax", ctypes.c_double), ("bx", ctypes.c_double), ("ay", ctypes.c_double), ("by", ctypes.c_double),
         ("gamma", ctypes.c_double), ("adv_x", ctypes.c_double), ("adv_y", ctypes.c_double),
         ("cfl", ctypes.c_double),
@@ -188,7 +188,7 @@ class MeshDesc:
     k: int = 2
     basis: int = BASIS_Q
     system: int = EULER
-    bc: int = PERIODIC
+    bc: object = PERIODIC  # one condition for every side, or (x-low, x-high, y-low, y-high)
     oe: int = 1
     rk: int = RK_SSP3
     ax: float = 0.0
@@ -200,10 +200,15 @@ class MeshDesc:
     adv_y: float = 0.0
     cfl: float = 0.1
 
+    @property
+    def sides(self):
+        b = self.bc
+        return tuple(b) if isinstance(b, (tuple, list)) else (b, b, b, b)
+
     def c(self) -> cdg_mesh_desc:
         return cdg_mesh_desc(self.dim, self.nx, self.ny if self.dim == 2 else 1, self.k, self.basis, self.system,
-                             self.bc, self.oe, self.rk, 0, self.ax, self.bx, self.ay, self.by, self.gamma,
-                             self.adv_x, self.adv_y, self.cfl)
+                             (ctypes.c_int * 4)(*self.sides), self.oe, self.rk, self.ax, self.bx, self.ay, self.by,
+                             self.gamma, self.adv_x, self.adv_y, self.cfl)
 
     @property
     def nfields(self) -> int:
@@ -217,7 +222,11 @@ class MeshDesc:
 
     @property
     def shape(self):
-        return (2, self.nfields, self.nmodes, self.ny if self.dim == 2 else 1, self.nx)
+        """The state's shape: both meshes in the padded layout, one more column
+        (row) where the low x (y) side is a reflective wall."""
+        nxs = self.nx + (self.sides[0] == REFLECTIVE)
+        nys = (self.ny + (self.sides[2] == REFLECTIVE)) if self.dim == 2 else 1
+        return (2, self.nfields, self.nmodes, nys, nxs)
 
 
 def desc_from_workload(w, **over) -> MeshDesc:

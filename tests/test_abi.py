@@ -56,7 +56,9 @@ def test_host_argument_checks_need_no_gpu():
     from paper_2503_12473_gb300 import oecdg as G
     L = G.load()
     EINVAL, EUNS = G.CDG_EINVAL, G.CDG_EUNSUPPORTED
-    cases = [(dict(dim=3), EINVAL), (dict(nx=1), EINVAL), (dict(ny=1), EINVAL), (dict(bc=2), EINVAL),
+    cases = [(dict(dim=3), EINVAL), (dict(nx=1), EINVAL), (dict(ny=1), EINVAL), (dict(bc=3), EINVAL),
+             (dict(bc=(G.PERIODIC, G.TRANSMISSIVE, G.PERIODIC, G.PERIODIC)), EINVAL),  # unpaired periodic side
+             (dict(bc=G.REFLECTIVE, system=G.ADVECTION), EINVAL), (dict(bc=G.REFLECTIVE, system=G.BURGERS), EINVAL),
              (dict(system=3), EINVAL), (dict(rk=0), EINVAL), (dict(rk=5), EINVAL), (dict(basis=2), EINVAL),
              (dict(k=0), EUNS), (dict(k=4), EUNS), (dict(bx=0.0), EINVAL), (dict(by=-1.0), EINVAL),
              (dict(cfl=0.0), EINVAL), (dict(gamma=1.0), EINVAL), (dict(nx=65536, ny=65536), EINVAL)]
@@ -70,7 +72,8 @@ def test_host_argument_checks_need_no_gpu():
     # the no-alloc OE: its own scope (Q^2 / P^2 advection and Euler) and scratch limit
     a, b = ctypes.c_void_p(16), ctypes.c_void_p(32)  # never dereferenced: the checks fail first
     for kw, want in [(dict(k=3), EUNS), (dict(basis=G.BASIS_P), EUNS), (dict(system=G.BURGERS), EUNS),
-                     (dict(nx=1), EINVAL), (dict(nx=2048, ny=2048), EINVAL)]:
+                     (dict(nx=1), EINVAL), (dict(nx=2048, ny=2048), EINVAL), (dict(bc=G.REFLECTIVE), EUNS),
+                     (dict(bc=(G.PERIODIC, G.PERIODIC, G.TRANSMISSIVE, G.TRANSMISSIVE)), EUNS)]:
         assert L.cdg_oe_damp_noalloc(ctypes.byref(_desc(**kw)), a, 0.1, b, None) == want, kw
     # the scratch limit, one block of 256 cells past it (the largest accepted
     # meshes run on the GPU in test_zz_no_alloc.py)

@@ -1,0 +1,134 @@
+"""Reflective walls and per-side boundary conditions on the CUDA path, against
+the oracle (whose wall closure is pinned to the mirror-extended periodic
+problem in test_oracle_reflective.py).
+
+Walls and mixed sides run on the degree-generic 2D kernels and on the 1D
+kernels, in the padded layout (the dual mesh's cell centred on a low-side
+wall in the slot after its last cell).  Checked: the sampling points (folded
+back across the walls) and the projection, then whole steps with the OE step,
+element by element (relative L1 per field <= 1e-9, the bar for discontinuous
+data; the data have a density step), for 1D and 2D Euler, P^k and Q^k,
+walls on every side, walls with periodic or outflow sides, and the
+persistent 1D launch.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_12473_gb300 import workloads as W
+from tests.test_oracle_reflective import _ic1, _ic2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+R, T, P = O.REFLECTIVE, O.TRANSMISSIVE, O.PERIODIC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2503_12473_gb300 import oecdg
+    oecdg.load()
+
+
+def _pair(dim, nx, ny, bc, k=2, basis=O.BASIS_Q, rk=3, by=0.75):
+    from paper_2503_12473_gb300 import oecdg as G
+    kw = dict(dim=dim, nx=nx, ny=ny if dim == 2 else 1, k=k, basis=basis, system=O.EULER, bc=bc, oe=1, rk=rk,
+              ax=0.0, bx=1.0, ay=0.0, by=by, gamma=1.4, cfl=0.1)
+    p = O.Problem(**kw)
+    d = G.MeshDesc(**{**kw, "adv_x": 1.0, "adv_y": 0.0})
+    assert tuple(d.shape) == p.shape
+    return p, d
+
+
+def _rel_l1(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).sum(axis=(0, 2, 3, 4)) / np.abs(b).sum(axis=(0, 2, 3, 4))
+
+
+CASES = [
+    ("1d-walls", 1, 40, 1, (R, R, P, P), 2, O.BASIS_Q, 3),
+    ("1d-wall-outflow", 1, 37, 1, (R, T, P, P), 2, O.BASIS_Q, 3),
+    ("1d-outflow-wall-p3-rk4", 1, 30, 1, (T, R, P, P), 3, O.BASIS_Q, 4),
+    ("2d-box-q2", 2, 12, 10, (R, R, R, R), 2, O.BASIS_Q, 3),
+    ("2d-walls-x-periodic-y-p2", 2, 10, 8, (R, R, P, P), 2, O.BASIS_P, 3),
+    ("2d-wall-outflow-q1-rk2", 2, 11, 9, (R, T, T, R), 1, O.BASIS_Q, 2),
+    ("2d-periodic-x-outflow-y-q2", 2, 12, 10, (P, P, T, T), 2, O.BASIS_Q, 3),
+]
+
+
+@pytest.mark.parametrize("name,dim,nx,ny,bc,k,basis,rk", CASES)
+def test_walls_and_mixed_sides_against_oracle(name, dim, nx, ny, bc, k, basis, rk):
+    from paper_2503_12473_gb300 import oecdg as G
+    p, d = _pair(dim, nx, ny, bc, k, basis, rk)
+    ic = _ic1 if dim == 1 else _ic2
+    ctx = G.Context(d)
+    # the sampling points, folded back across the walls, and the projection
+    n = ctx.cdg_quad_points(None)
+    xy = torch.empty((n, dim), dtype=torch.float64, device="cuda")
+    ctx.cdg_quad_points(xy)
+    pts = O.quad_points(p)
+    assert pts.shape == (n, dim)
+    np.testing.assert_allclose(xy.cpu().numpy(), pts, rtol=0, atol=1e-14)
+    ug = ctx.project(ic)
+    uo = O.project_fn(p, ic)
+    assert _rel_l1(ug.cpu().numpy(), uo).max() < 1e-13
+    # whole steps with the OE step
+    steps = 6
+    ctx.cdg_step(ug, 0.0, 0.0, steps)
+    ref, t, done, st = O.advance(p, uo, 0.0, 0.0, steps)
+    assert st == O.OK and done == steps
+    assert abs(ctx.cdg_get_time() - t) <= 1e-13 * t
+    got = ug.cpu().numpy()
+    assert np.isfinite(got).all()
+    err = _rel_l1(got, ref)
+    assert err.max() < 1e-9, (name, err)
+    if bc[0] == R:  # the primal mesh's unused slot stays 0
+        assert np.all(got[0, ..., nx:] == 0.0)
+
+
+def test_persistent_1d_with_walls():
+    """The persistent 1D launch with a wall and an outflow side equals the
+    per-kernel steps to rounding and the oracle at the parity bar."""
+    from paper_2503_12473_gb300 import oecdg as G
+    p, d = _pair(1, 64, 1, (R, T, P, P))
+    ctx = G.Context(d)
+    u0 = ctx.project(_ic1)
+    a = u0.clone()
+    b = u0.clone()
+    ctx.cdg_step_async(a, 0.0, 0.0, 20)
+    ctx.cdg_step_persistent(b, 0.0, 0.0, 20)
+    assert ctx.cdg_check_status() == G.CDG_OK
+    num = (a - b).abs().amax(dim=(0, 2, 3, 4))
+    den = a.abs().amax(dim=(0, 2, 3, 4))
+    assert (num / den).max().item() <= 1e-13
+    ref, *_ = O.advance(p, O.project_fn(p, _ic1), 0.0, 0.0, 20)
+    assert _rel_l1(b.cpu().numpy(), ref).max() < 1e-9
+
+
+def test_wall_closes_the_box():
+    """A box closed by walls on every side conserves mass and energy: the
+    weighted cell averages of both meshes (wall-centred dual cells count by
+    the part of them inside) keep their sums to rounding over 50 steps."""
+    from paper_2503_12473_gb300 import oecdg as G
+    p, d = _pair(2, 16, 12, (R, R, R, R))
+    ctx = G.Context(d)
+    u = ctx.project(_ic2)
+
+    def totals(v):
+        v = v.cpu().numpy()
+        w = np.ones((2, 13, 17))
+        w[0, 12, :] = w[0, :, 16] = 0.0           # unused primal slots
+        w[1, :, 16] *= 0.5                        # centred on x = 0
+        w[1, :, 15] *= 0.5                        # centred on x = 1
+        w[1, 12, :] *= 0.5                        # centred on y = 0
+        w[1, 11, :] *= 0.5                        # centred on y = 0.75
+        return [(v[:, f, 0] * w).sum() for f in (0, 3)]
+
+    m0 = totals(u)
+    ctx.cdg_step(u, 0.0, 0.0, 50)
+    m1 = totals(u)
+    for a, b in zip(m0, m1):
+        assert abs(a - b) <= 1e-12 * abs(a)
