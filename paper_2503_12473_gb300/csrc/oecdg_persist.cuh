@@ -103,20 +103,41 @@ struct SigmaNorm {
 
 // avg and sigma of one (mesh, field) from the block partials [2][nblk][F][3]
 // (sum of weighted cell averages, max, min), by one full warp in a fixed
-// order: lane l folds partials l, l + 32, ...; then a shuffle tree.
-// avg = sum / ncell (0 for an odd field), sigma = max(max - avg, avg - min)
-// (Section 2.2, sigma_K).
+// order: lane l folds partials l + 32 r + 256 q into accumulator r (r = 0..7,
+// eight independent chains, so that the loads overlap), the accumulators are
+// folded r = 0..7, then a shuffle tree.  avg = sum / ncell (0 for an odd
+// field), sigma = max(max - avg, avg - min) (Section 2.2, sigma_K).
 template <int LD>
 __device__ __forceinline__ void warp_sigma(const double* part, long long nblk, int F, int mesh, int f,
                                            const SigmaNorm& sn, double* avg, double* sigma) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  double s = 0.0, mx = -__builtin_huge_val(), mn = __builtin_huge_val();
-  for (long long b = lane; b < nblk; b += 32) {
-    const double* p = part + ((mesh * nblk + b) * F + f) * 3;
-    s += ldv<LD>(p);
-    mx = fmax(mx, ldv<LD>(p + 1));
-    mn = fmin(mn, ldv<LD>(p + 2));
+  constexpr int CH = 8;
+  double sr[CH], xr[CH], nr[CH];
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    sr[r] = 0.0;
+    xr[r] = -__builtin_huge_val();
+    nr[r] = __builtin_huge_val();
+  }
+  for (long long b0 = lane; b0 < nblk; b0 += 32 * CH) {
+#pragma unroll
+    for (int r = 0; r < CH; ++r) {
+      const long long b = b0 + 32 * r;
+      if (b < nblk) {
+        const double* p = part + ((mesh * nblk + b) * F + f) * 3;
+        sr[r] += ldv<LD>(p);
+        xr[r] = fmax(xr[r], ldv<LD>(p + 1));
+        nr[r] = fmin(nr[r], ldv<LD>(p + 2));
+      }
+    }
+  }
+  double s = sr[0], mx = xr[0], mn = nr[0];
+#pragma unroll
+  for (int r = 1; r < CH; ++r) {
+    s += sr[r];
+    mx = fmax(mx, xr[r]);
+    mn = fmin(mn, nr[r]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

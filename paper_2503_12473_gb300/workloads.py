@@ -19,6 +19,10 @@ Workloads (sizes and data):
   * ``batched_2d``    -- 256 periodic 2D Euler problems with seeded sizes and data.
   * ``vortex_2d``     -- isentropic vortex (strength 5) on uniform flow (1,1),
     [0,10]^2 periodic, 256^2.
+  * ``two_blast_waves_1d`` -- 1D Euler, [0, 1] between reflective walls, 960
+    cells, P^2, SSP-RK3, CFL 0.3 (Section 4's value for P^2 on discontinuous
+    data), (rho, v, p) = (1, 0, 1e3) for x < 0.1, (1, 0, 1e-2) in between,
+    (1, 0, 1e2) for x > 0.9 (the two-blast-wave data of Section 4), T = 0.038.
 """
 from __future__ import annotations
 
@@ -33,7 +37,7 @@ GAMMA = 1.4
 # system / basis / boundary codes shared by the two sides' problem descriptions
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BASIS_Q, BASIS_P = 0, 1
-PERIODIC, TRANSMISSIVE = 0, 1
+PERIODIC, TRANSMISSIVE, REFLECTIVE = 0, 1, 2
 
 
 @dataclass
@@ -71,8 +75,18 @@ class Workload:
         return (self.k + 1) ** 2 if self.basis == BASIS_Q else (self.k + 1) * (self.k + 2) // 2
 
     @property
+    def sides(self):
+        """Boundary condition of each side (x-low, x-high, y-low, y-high)."""
+        b = self.bc
+        return tuple(b) if isinstance(b, (tuple, list)) else (b, b, b, b)
+
+    @property
     def state_shape(self):
-        return (2, self.nfields, self.nmodes, self.ny if self.dim == 2 else 1, self.nx)
+        """Both meshes in the padded layout: one more column (row) where the low
+        x (y) side is a reflective wall (the dual cell centred on it)."""
+        nxs = self.nx + (self.sides[0] == REFLECTIVE)
+        nys = (self.ny + (self.sides[2] == REFLECTIVE)) if self.dim == 2 else 1
+        return (2, self.nfields, self.nmodes, nys, nxs)
 
     @property
     def dofs(self) -> int:
@@ -130,6 +144,16 @@ def shu_osher(gamma=GAMMA):
         v = np.where(left, 2.629369, 0.0)
         p = np.where(left, 10.33333, 1.0)
         return prim_to_cons_1d(rho, v, p, gamma)
+    return f
+
+
+def two_blast_waves(gamma=GAMMA):
+    """(rho, v, p) = (1, 0, 1e3) for x < 0.1, (1, 0, 1e-2) for 0.1 < x < 0.9,
+    (1, 0, 1e2) for x > 0.9."""
+    def f(xy):
+        x = np.asarray(xy, dtype=np.float64).reshape(len(xy), -1)[:, 0]
+        p = np.where(x < 0.1, 1e3, np.where(x > 0.9, 1e2, 1e-2))
+        return prim_to_cons_1d(np.ones_like(x), np.zeros_like(x), p, gamma)
     return f
 
 
@@ -280,6 +304,11 @@ def advection_1d(n: int = 128) -> Workload:
 def shu_osher_1d(n: int = 4000) -> Workload:
     return Workload("euler_1d_shu_osher_p2_4000", 1, n, 1, 2, EULER, TRANSMISSIVE, -5.0, 5.0, cfl=0.1, T=1.8,
                     u0=shu_osher())
+
+
+def two_blast_waves_1d(n: int = 960) -> Workload:
+    return Workload(f"euler_1d_two_blast_waves_p2_{n}", 1, n, 1, 2, EULER, (REFLECTIVE, REFLECTIVE, PERIODIC, PERIODIC),
+                    0.0, 1.0, cfl=0.3, T=0.038, u0=two_blast_waves())
 
 
 def burgers_1d(n: int = 128, k: int = 3) -> Workload:

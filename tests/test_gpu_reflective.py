@@ -132,3 +132,25 @@ def test_wall_closes_the_box():
     m1 = totals(u)
     for a, b in zip(m0, m1):
         assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_two_blast_waves_flag_a_nonphysical_average_like_the_oracle():
+    """Section 4's two-blast-wave data (pressure 1e3 | 1e-2 | 1e2 between
+    reflective walls, P^2, 960 cells, CFL 0.3) without the positivity-
+    preserving limiter the paper cites for other tests: the P^2 projection of
+    the 1e5 pressure jump undershoots, and after the first step a cell average
+    beside it has negative pressure.  Both sides report it after the same
+    step (CDG_ENONPHYSICAL; its wave speed taken as 0), and their states after
+    that step still agree."""
+    from paper_2503_12473_gb300 import oecdg as G
+    w = W.two_blast_waves_1d(960)
+    d = G.desc_from_workload(w)
+    p = O.Problem(dim=1, nx=w.nx, ny=1, k=2, system=O.EULER, bc=w.bc, oe=1, rk=3, ax=w.ax, bx=w.bx, cfl=w.cfl)
+    ctx = G.Context(d)
+    u0 = O.project_fn(p, w.u0)
+    ug = torch.from_numpy(u0).cuda()
+    ctx.cdg_step_async(ug, 0.0, w.T, 1)
+    assert ctx.cdg_check_status() == G.CDG_ENONPHYSICAL
+    ref, t, done, st = O.advance(p, u0, 0.0, w.T, 1)
+    assert st == O.ENONPHYSICAL and done == 1
+    assert _rel_l1(ug.cpu().numpy(), ref).max() < 1e-9
