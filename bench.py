@@ -325,13 +325,26 @@ def run_ours(args, ws, rank, local):
 
 
 # Executed FP64 flops (2 DFMA + DADD + DMUL) and DRAM bytes per cell of the
-# degree-generic 2D kernels, 2D Euler, periodic, one 512^2 launch each; keys
-# (k, basis).  Empty: the earlier ncu counts were taken before these kernels
-# moved to the seeded reciprocal and square root (fewer flops per cell), so
-# their lines report achieved and frac as null until the kernels are counted
-# again.
-FLOPS_PER_CELL_2K = {}
-TRAFFIC_PER_CELL_2K = {}
+# degree-generic 2D kernels, 2D Euler steady wave, periodic, 512^2; keys
+# (k, basis).  Each figure is the mean over the launches of one step (the
+# (k+1)-order RK method's 2, 3 or 4 stage and OE launches) of one ncu capture of
+# the FP64 instruction counters and dram__bytes_read + write, divided by the
+# 2 x 512^2 cells of a launch.  The P^1, P^2 and Q^1 states (50-101 MB) fit in
+# L2, so their DRAM bytes fall below the algorithmic state traffic.
+FLOPS_PER_CELL_2K = {
+    (1, "P"): {"stage": 3309, "oe": 2601},
+    (2, "P"): {"stage": 9523, "oe": 6875},
+    (3, "P"): {"stage": 21711, "oe": 15126},
+    (1, "Q"): {"stage": 3287, "oe": 3062},
+    (3, "Q"): {"stage": 24694, "oe": 21542},
+}
+TRAFFIC_PER_CELL_2K = {
+    (1, "P"): {"stage": 293, "oe": 208},
+    (2, "P"): {"stage": 704, "oe": 545},
+    (3, "P"): {"stage": 1593, "oe": 954},
+    (1, "Q"): {"stage": 374, "oe": 284},
+    (3, "Q"): {"stage": 2191, "oe": 1510},
+}
 
 
 def run_generic(args, ws, rank, local):
