@@ -504,7 +504,14 @@ static int odd_field(const orc_problem* p, int f) {
  * With reflective walls Omega is the mirror-extended domain: wall-centred dual
  * cells count half in the average, a normal momentum has average 0 (its mirror
  * image is its negative), and the max of |u - avg| over the mirror images
- * equals that over the stored cells. */
+ * equals that over the stored cells.
+ * Reading of "sigma_K = 0" in floating point: a field that is constant in exact
+ * arithmetic (a uniform density) carries rounding noise of an ulp or two in its
+ * point values and in the rounded average, so its computed sigma is a few ulps
+ * and the jumps it is divided into are of the same size; the ratio would damp
+ * as hard as a shock.  A sigma at or below 2^-40 max|u| (max over the same
+ * points, 4096 ulps of the field's magnitude) is therefore taken as 0. */
+#define ORC_SIGMA_FLOOR 0x1p-40
 static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg, real* sig) {
   int F = nfields(p), nq = p->k + 1, d = p->dim;
   double gx[ORC_MAXQ], gw[ORC_MAXQ];
@@ -542,10 +549,12 @@ static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg,
     avg[f] = odd_field(p, f) ? 0.0 : tot[f] / vol;
     sig[f] = 0.0;
   }
-  /* the max of |u - avg| over all points (order-independent) */
+  /* the max of |u - avg| and of |u| over all points (order-independent) */
+  double mag[ORC_MAXF] = {0};
 #pragma omp parallel
   {
     real loc[ORC_MAXF] = {0};
+    double lmag[ORC_MAXF] = {0};
     real v[ORC_MAXF];
 #pragma omp for schedule(static)
     for (int j = 0; j < cy; ++j)
@@ -556,12 +565,17 @@ static void mesh_sigma(const orc_problem* p, const real* u, int mesh, real* avg,
             for (int f = 0; f < F; ++f) {
               real e = R_ABS(v[f] - avg[f]);
               if (RE(e) > RE(loc[f])) loc[f] = e;
+              if (fabs(RE(v[f])) > lmag[f]) lmag[f] = fabs(RE(v[f]));
             }
           }
 #pragma omp critical
-    for (int f = 0; f < F; ++f)
+    for (int f = 0; f < F; ++f) {
       if (RE(loc[f]) > RE(sig[f])) sig[f] = loc[f];
+      if (lmag[f] > mag[f]) mag[f] = lmag[f];
+    }
   }
+  for (int f = 0; f < F; ++f)
+    if (RE(sig[f]) <= ORC_SIGMA_FLOOR * mag[f]) sig[f] = 0.0;
 }
 
 static double factorial(int m) {

@@ -38,10 +38,11 @@ __global__ void __launch_bounds__(NT, OECDG_STAGE_MINB) k_stage2d(Geo g, const d
 // Fixed-order reduction of the block partials: avg and sigma per mesh and
 // field (Section 2.2): avg = mean of the cell averages over the stored cells,
 // sigma = max(max - avg, avg - min) over the cell Gauss points.  grid = (F, 2),
-// one warp each: the same code as the persistent kernels' sigma phase.
+// 256 threads each (block_sigma): the same summation order, bit for bit, as the
+// one warp per (mesh, field) of the persistent kernels' sigma phase.
 __global__ void k_sigma(const double* __restrict__ partials, long long nblk, int F, SigmaNorm sn,
                         double* __restrict__ sigma, double* __restrict__ avg) {
-  warp_sigma<LD_NC>(partials, nblk, F, blockIdx.y, blockIdx.x, sn, avg, sigma);
+  block_sigma<LD_NC>(partials, nblk, F, blockIdx.y, blockIdx.x, sn, avg, sigma);
 }
 
 // ---------------------------------------------------------------- OE step --
@@ -103,17 +104,20 @@ __global__ void k_wave2d(Geo g, const double* __restrict__ u, double* __restrict
   }
 }
 
-// One thread: the maxima of the block partials, then finish_dt (tau_max, the
-// clipped tau, the time).
+// One block: the maxima of the block partials (exact in any order), then
+// finish_dt (tau_max, the clipped tau, the time) by thread 0.
 __global__ void k_dt_final(const double* __restrict__ partial, int nblk, double hx, double hy, int dim, double cfl,
                            double T_end, double* __restrict__ dt, double* __restrict__ time) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double sh[32];
   double bx = 0.0, by = 0.0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
     bx = fmax(bx, partial[2 * b]);
     by = fmax(by, partial[2 * b + 1]);
   }
-  finish_dt(bx, by, hx, hy, dim, cfl, T_end, dt, time);
+  bx = block_reduce_max(bx, sh);
+  __syncthreads();
+  by = block_reduce_max(by, sh);
+  if (threadIdx.x == 0) finish_dt(bx, by, hx, hy, dim, cfl, T_end, dt, time);
 }
 
 __global__ void k_set2(double* __restrict__ p, double a, double b) {
@@ -207,7 +211,7 @@ cudaError_t launch_stage2d(int sys, int bc, const Geo& g, int rhs_only, const do
 
 cudaError_t launch_sigma(const double* partials, long long nblk, int F, const SigmaNorm& sn, double* sigma,
                          double* avg, cudaStream_t st) {
-  k_sigma<<<dim3(F, 2), 32, 0, st>>>(partials, nblk, F, sn, sigma, avg);
+  k_sigma<<<dim3(F, 2), 256, 0, st>>>(partials, nblk, F, sn, sigma, avg);
   return cudaGetLastError();
 }
 
@@ -246,13 +250,13 @@ cudaError_t launch_dt2d(int sys, const Geo& g, const double* u, double* partial,
                         double* dt, double* time, int* status, cudaStream_t st) {
   if (sys == SYS_EULER) k_wave2d<SYS_EULER><<<nblk, 256, 0, st>>>(g, u, partial, status);
   else k_wave2d<SYS_ADV><<<nblk, 256, 0, st>>>(g, u, partial, status);
-  k_dt_final<<<1, 32, 0, st>>>(partial, nblk, g.hx, g.hy, 2, g.cfl, T_end, dt, time);
+  k_dt_final<<<1, 256, 0, st>>>(partial, nblk, g.hx, g.hy, 2, g.cfl, T_end, dt, time);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dt_final(const double* partial, int nblk, double hx, double hy, int dim, double cfl, double T_end,
                             double* dt, double* time, cudaStream_t st) {
-  k_dt_final<<<1, 32, 0, st>>>(partial, nblk, hx, hy, dim, cfl, T_end, dt, time);
+  k_dt_final<<<1, 256, 0, st>>>(partial, nblk, hx, hy, dim, cfl, T_end, dt, time);
   return cudaGetLastError();
 }
 

@@ -464,7 +464,7 @@ __global__ void k_sigma_stats_final(const double* __restrict__ part, long long n
   o[2] = kmx;
   o[3] = mn;
   o[4] = kmn;
-  o[5] = fmax(mx - a, a - mn);
+  o[5] = sigma_from_range(mx, mn, a);
 }
 
 // ------------------------------------------------------------- OE adjoint --

@@ -19,6 +19,23 @@ enum { BASIS_Q = 0, BASIS_P = 1 };
 // status bits written by kernels
 enum { ST_NONPHYSICAL = 1 };
 
+// sigma_K of one (mesh, field) (Section 2.2): ||u_h - avg(u_h)||_inf over the
+// domain, from the maximum mx and the minimum mn of the point values and the
+// domain average a, = max(mx - a, a - mn).  The OE coefficients divide by it
+// and vanish where it is 0, which in exact arithmetic is a constant field.  A
+// field that is constant up to rounding (the uniform density of a blast-wave
+// start: every point value within an ulp or two of 1) instead has a sigma of a
+// few ulps, whose value depends on how the average was rounded, and jumps of
+// the same size: their ratio would damp every field of every cell as hard as a
+// shock.  So a sigma at or below 2^-40 of the field's magnitude
+// max(|mx|, |mn|) (4096 ulps) counts as 0.
+constexpr double SIGMA_FLOOR = 0x1p-40;
+
+__host__ __device__ __forceinline__ double sigma_from_range(double mx, double mn, double a) {
+  const double s = fmax(mx - a, a - mn);
+  return s <= SIGMA_FLOOR * fmax(fabs(mx), fabs(mn)) ? 0.0 : s;
+}
+
 // 3-point Gauss-Legendre rule on [-1, 1]: nodes -sqrt(3/5), 0, sqrt(3/5),
 // weights 5/9, 8/9, 5/9.
 constexpr double GQ = 0.77459666924148337704;  // sqrt(3/5)

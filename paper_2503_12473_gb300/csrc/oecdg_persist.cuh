@@ -106,7 +106,8 @@ struct SigmaNorm {
 // order: lane l folds partials l + 32 r + 256 q into accumulator r (r = 0..7,
 // eight independent chains, so that the loads overlap), the accumulators are
 // folded r = 0..7, then a shuffle tree.  avg = sum / ncell (0 for an odd
-// field), sigma = max(max - avg, avg - min) (Section 2.2, sigma_K).
+// field), sigma = max(max - avg, avg - min) (Section 2.2, sigma_K; 0 at the
+// rounding level of the field, sigma_from_range).
 template <int LD>
 __device__ __forceinline__ void warp_sigma(const double* part, long long nblk, int F, int mesh, int f,
                                            const SigmaNorm& sn, double* avg, double* sigma) {
@@ -148,7 +149,51 @@ __device__ __forceinline__ void warp_sigma(const double* part, long long nblk, i
   if (lane == 0) {
     const double a = ((sn.odd >> f) & 1) ? 0.0 : s / sn.ncell[mesh];
     avg[mesh * F + f] = a;
-    sigma[mesh * F + f] = fmax(mx - a, a - mn);
+    sigma[mesh * F + f] = sigma_from_range(mx, mn, a);
+  }
+}
+
+// The same reduction as warp_sigma, bit for bit, by the 8 warps of one block
+// of 256 threads: warp r runs accumulator chain r (partials lane + 32 r + 256 q,
+// q = 0, 1, ..., in that order), then warp 0 folds the chains r = 0..7 of its
+// lane and runs the same shuffle tree.  For the per-phase launch, where the
+// single warp's 8 chains of L2 round trips would dominate the kernel.
+template <int LD>
+__device__ __forceinline__ void block_sigma(const double* part, long long nblk, int F, int mesh, int f,
+                                            const SigmaNorm& sn, double* avg, double* sigma) {
+  constexpr int CH = 8;
+  __shared__ double sh[3][CH][32];
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  double sr = 0.0, xr = -__builtin_huge_val(), nr = __builtin_huge_val();
+  for (long long b = lane + 32 * r; b < nblk; b += 32 * CH) {
+    const double* p = part + ((mesh * nblk + b) * F + f) * 3;
+    sr += ldv<LD>(p);
+    xr = fmax(xr, ldv<LD>(p + 1));
+    nr = fmin(nr, ldv<LD>(p + 2));
+  }
+  sh[0][r][lane] = sr;
+  sh[1][r][lane] = xr;
+  sh[2][r][lane] = nr;
+  __syncthreads();
+  if (r != 0) return;
+  const unsigned full = 0xffffffffu;
+  double s = sh[0][0][lane], mx = sh[1][0][lane], mn = sh[2][0][lane];
+#pragma unroll
+  for (int q = 1; q < CH; ++q) {
+    s += sh[0][q][lane];
+    mx = fmax(mx, sh[1][q][lane]);
+    mn = fmin(mn, sh[2][q][lane]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(full, s, o);
+    mx = fmax(mx, __shfl_down_sync(full, mx, o));
+    mn = fmin(mn, __shfl_down_sync(full, mn, o));
+  }
+  if (lane == 0) {
+    const double a = ((sn.odd >> f) & 1) ? 0.0 : s / sn.ncell[mesh];
+    avg[mesh * F + f] = a;
+    sigma[mesh * F + f] = sigma_from_range(mx, mn, a);
   }
 }
 
