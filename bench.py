@@ -50,10 +50,10 @@ HBM_FALLBACK_GBS = 6800.0
 # cell, the other two 7,014: the figure is their mean over a step.  Source: an
 # ncu capture of the FP64 instruction counters of the three stage and three OE
 # launches of one 512^2 step.
-FLOPS_PER_CELL = {"stage": 6990, "oe": 6065}
+FLOPS_PER_CELL = {"stage": 6990, "oe": 5900}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture,
 # mean over the step's launches); None once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 822, "oe": 500}
+TRAFFIC_PER_CELL = {"stage": 808, "oe": 500}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
 # (neighbour re-reads, of both meshes, are L2 hits: the two meshes' blocks of a
@@ -332,18 +332,18 @@ def run_ours(args, ws, rank, local):
 # 2 x 512^2 cells of a launch.  The P^1, P^2 and Q^1 states (50-101 MB) fit in
 # L2, so their DRAM bytes fall below the algorithmic state traffic.
 FLOPS_PER_CELL_2K = {
-    (1, "P"): {"stage": 3309, "oe": 2601},
-    (2, "P"): {"stage": 9523, "oe": 6875},
-    (3, "P"): {"stage": 21711, "oe": 15126},
-    (1, "Q"): {"stage": 3287, "oe": 3062},
-    (3, "Q"): {"stage": 24694, "oe": 21542},
+    (1, "P"): {"stage": 3309, "oe": 2511},
+    (2, "P"): {"stage": 9523, "oe": 6785},
+    (3, "P"): {"stage": 21711, "oe": 15164},
+    (1, "Q"): {"stage": 3287, "oe": 2983},
+    (3, "Q"): {"stage": 24694, "oe": 21492},
 }
 TRAFFIC_PER_CELL_2K = {
-    (1, "P"): {"stage": 293, "oe": 208},
-    (2, "P"): {"stage": 704, "oe": 545},
-    (3, "P"): {"stage": 1593, "oe": 954},
-    (1, "Q"): {"stage": 374, "oe": 284},
-    (3, "Q"): {"stage": 2191, "oe": 1510},
+    (1, "P"): {"stage": 293, "oe": 196},
+    (2, "P"): {"stage": 704, "oe": 614},
+    (3, "P"): {"stage": 1593, "oe": 1271},
+    (1, "Q"): {"stage": 374, "oe": 285},
+    (3, "Q"): {"stage": 2191, "oe": 1509},
 }
 
 

@@ -60,9 +60,11 @@ template <int SYS, int BC, bool WRITE_DELTA, bool ISO>
 __global__ void __launch_bounds__(NT, OECDG_OE_MINB) k_oe2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                              const double* __restrict__ dt, const double* __restrict__ sigma,
                                              double* __restrict__ delta_out, int* __restrict__ status) {
+  __shared__ double isg[Fields<SYS>::F];
+  oe_inv_sigma<Fields<SYS>::F>(sigma, blockIdx.x & 1, isg);
   oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.x & 1,
                                           (blockIdx.x >> 1) * TX + (threadIdx.x % TX),
-                                          blockIdx.y * TY + (threadIdx.x / TX));
+                                          blockIdx.y * TY + (threadIdx.x / TX), nullptr, isg);
 }
 
 // ------------------------------------------------------------- time step --

@@ -350,6 +350,8 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 
 // REC = 1 also records, per cell and order m, (delta^m, the field that gives
 // the max, that field's x- and y-face sums) for the adjoint: rec[cell][3][4].
+// isg (optional): 1/sigma of this mesh's fields (0 where sigma = 0), taken
+// once per block by the caller (oe_inv_sigma) instead of once per cell.
 // ISO = true requires hx == hy: every m-th derivative then carries the same
 // factor (2/h)^m, so the traces stay in reference units and the factor is
 // applied once, in the constants of delta^m (the recorded sums are physical).
@@ -357,7 +359,8 @@ template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false, int 
 __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
-                                          int j, double* __restrict__ rec = nullptr) {
+                                          int j, double* __restrict__ rec = nullptr,
+                                          const double* __restrict__ isg = nullptr) {
   constexpr int F = Fields<SYS>::F;
   if (i >= g.nx || j >= g.ny) return;
   const long long P = g.plane;
@@ -388,12 +391,12 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     by = fabs(g.adv_y);
   }
   // (2m+1) h^{m-1} / ((2k-1) m!) / 4  (1/4: the half-face rule over |e|)
-  const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;  // reference -> physical derivative
+  const double dx1 = g.i2x, dy1 = g.i2y;  // reference -> physical derivative: 2/hx, 2/hy
   // ISO: the face sums of orders 1 and 2 are in reference units; their
   // physical factors dx1 and dx1^2 join the constants
   const double iso1 = ISO ? dx1 : 1.0, iso2 = ISO ? dx1 * dx1 : 1.0;
-  const double cx0 = 1.0 / (12.0 * g.hx), cx1 = 0.25 * iso1, cx2 = 5.0 * g.hx / 24.0 * iso2;
-  const double cy0 = 1.0 / (12.0 * g.hy), cy1 = 0.25 * iso1, cy2 = 5.0 * g.hy / 24.0 * iso2;
+  const double cx0 = g.i12x, cx1 = 0.25 * iso1, cx2 = g.h24x5 * iso2;  // 1/(12 hx), 5 hx/24
+  const double cy0 = g.i12y, cy1 = 0.25 * iso1, cy2 = g.h24y5 * iso2;
 
   double d0 = 0.0, d1 = 0.0, d2 = 0.0;  // max over fields
   int rf[3] = {-1, -1, -1};             // REC: field of the max, and its face sums
@@ -413,24 +416,40 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     // dl = 1 - 2 h (h = the half), re-expanded in t with
     //   P_1(t + dl) = P_1(t) + dl,  P_2(t + dl) = P_2(t) + 3 dl P_1(t) + 3/2.
     // The difference series (u_K - w) is then scaled to physical derivatives
-    // and evaluated at the half-face's Gauss points.
+    // and evaluated at the half-face's Gauss points; the weighted point values
+    // accumulate straight into the direction's face sums (12 points each).
+    // Two coefficients are formed already multiplied by 3, where the factor
+    // is needed (3 e0_2 for the tangential derivative, ISO: 3 e2_0 for the
+    // second normal derivative), from 3 x K's coefficient taken once per
+    // direction: one FMA per half-face instead of a subtraction and a product.
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
       const double dn1 = n == 0 ? dx1 : dy1, dt1 = n == 0 ? dy1 : dx1;  // normal / tangential scales
       const double dn2 = dn1 * dn1, dt2 = dt1 * dt1;
+      double& A0 = n == 0 ? Sx0 : Sy0;
+      double& A1 = n == 0 ? Sx1 : Sy1;
+      double& A2 = n == 0 ? Sx2 : Sy2;
+      // K's coefficients (normal degree a = 0, 1, 2; tangential degree t)
+      double k02[3], k1[3], k2[3];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const double u0 = n == 0 ? u[t * 3] : u[t];
+        k1[t] = n == 0 ? u[t * 3 + 1] : u[3 + t];
+        k2[t] = n == 0 ? u[t * 3 + 2] : u[6 + t];
+        k02[t] = u0 + k2[t];  // P_0 + P_2 at either side (P_2(+-1) = 1)
+      }
+      const double k02x3 = 3.0 * k02[2];
+      const double k2x3 = 3.0 * k2[0];  // ISO: 3 c2_0
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const double s = 2.0 * side - 1.0;
-        double c0[3], c1[3], c2[3];
+        double c0[2], c1[3];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          // coefficient (normal degree a, tangential degree t)
-          const double u0 = n == 0 ? u[t * 3] : u[t], u1 = n == 0 ? u[t * 3 + 1] : u[3 + t];
-          const double u2 = n == 0 ? u[t * 3 + 2] : u[6 + t];
-          c0[t] = u0 + s * u1 + u2;
-          c1[t] = fma(3.0 * s, u2, u1);
-          c2[t] = u2;  // the second normal derivative is 3 c2; the 3 is applied below
-        }
+        for (int t = 0; t < 2; ++t) c0[t] = k02[t] + s * k1[t];
+        const double c0x3 = fma(3.0 * s, k1[2], k02x3);  // 3 c0_2
+#pragma unroll
+        for (int t = 0; t < 3; ++t) c1[t] = fma(3.0 * s, k2[t], k1[t]);
+        const double* c2 = k2;  // the second normal derivative is 3 c2; the 3 is applied below
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const double dl = 1.0 - 2.0 * h;
@@ -448,9 +467,9 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
           const double* o1 = w1;
           const double* o2 = w2;  // (second normal derivative) / 3
-          // difference series in K's tangential coordinate
-          double e0[3], e1[3], e2[3];
-          e0[2] = c0[2] - o0[2];
+          // difference series in K's tangential coordinate (e0_2 as 3 e0_2)
+          double e0[2], e1[3], e2[3];
+          const double e02x3 = fma(-3.0, o0[2], c0x3);
           e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
           e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
           e1[2] = c1[2] - o1[2];
@@ -458,7 +477,6 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           e1[0] = c1[0] - fma(1.5, o1[2], fma(dl, o1[1], o1[0]));
           e2[2] = c2[2] - o2[2];
           e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
-          e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
           // physical scalings: normal derivative series (order 1, 2), tangential
           // derivative of the value and of the normal derivative, second
           // tangential derivative (a constant on the half-face)
@@ -467,49 +485,41 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           // go into the points' constant coefficients, see hn and hm below)
           if constexpr (ISO) {
             a0 = e1[0], a1 = e1[1], a2 = e1[2];
-            b0 = 3.0 * e2[0], b1 = e2[1], b2 = e2[2];
-            t0 = e0[1], t1 = 3.0 * e0[2];
+            b0 = fma(-4.5, o2[2], fma(-3.0 * dl, o2[1], fma(-3.0, o2[0], k2x3)));  // 3 e2_0
+            b1 = e2[1], b2 = e2[2];
+            t0 = e0[1], t1 = e02x3;
             m0 = a1, m1 = a2;
             tt = t1;
           } else {
             const double dn2x3 = 3.0 * dn2;
+            e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
             a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
             b0 = dn2x3 * e2[0], b1 = dn2x3 * e2[1], b2 = dn2x3 * e2[2];
-            t0 = dt1 * e0[1], t1 = 3.0 * dt1 * e0[2];
+            t0 = dt1 * e0[1], t1 = dt1 * e02x3;
             m0 = dt1 * a1, m1 = 3.0 * dt1 * a2;
-            tt = 3.0 * dt2 * e0[2];
+            tt = dt2 * e02x3;
           }
           const double tt2 = fma(tt, tt, SQ_FLOOR);
-          double S0 = 0.0, S1 = 0.0, S2 = 0.0;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const double ts = xs_self(h, q);
             const double p2 = lp(2, ts);
-            const double v = fma(p2, e0[2], fma(ts, e0[1], e0[0]));   // u_K - w
-            const double gn = fma(p2, a2, fma(ts, a1, a0));           // normal derivative
-            const double gt = fma(ts, t1, t0);                        // tangential derivative
+            const double v = fma(p2 / 3.0, e02x3, fma(ts, e0[1], e0[0]));  // u_K - w
+            const double gn = fma(p2, a2, fma(ts, a1, a0));                 // normal derivative
+            const double gt = fma(ts, t1, t0);                              // tangential derivative
             const double hn = ISO ? fma(3.0 * p2, b2, fma(3.0 * ts, b1, b0))  // second normal
                                   : fma(p2, b2, fma(ts, b1, b0));
             const double hm = ISO ? fma(3.0 * ts, m1, m0) : fma(ts, m1, m0);  // mixed
-            S0 = fma(gwt(q), fabs(v), S0);
-            S1 = fma(gwt(q), sqrt_pos(fma(gn, gn, fma(gt, gt, SQ_FLOOR))), S1);
-            S2 = fma(gwt(q), sqrt_pos(fma(hn, hn, fma(hm, hm, tt2))), S2);
-          }
-          if (n == 0) {
-            Sx0 += S0;
-            Sx1 += S1;
-            Sx2 += S2;
-          } else {
-            Sy0 += S0;
-            Sy1 += S1;
-            Sy2 += S2;
+            A0 = fma(gwt(q), fabs(v), A0);
+            A1 = fma(gwt(q), sqrt_pos(fma(gn, gn, fma(gt, gt, SQ_FLOOR))), A1);
+            A2 = fma(gwt(q), sqrt_pos(fma(hn, hn, fma(hm, hm, tt2))), A2);
           }
         }
       }
     }
     if (sg != 0.0) {
       // explicit fma: the recording and the plain instantiation must round alike
-      const double is = 1.0 / sg;
+      const double is = isg ? isg[f] : 1.0 / sg;
       const double v0 = fma(bx * cx0, Sx0, (by * cy0) * Sy0) * is;
       const double v1 = fma(bx * cx1, Sx1, (by * cy1) * Sy1) * is;
       const double v2 = fma(bx * cx2, Sx2, (by * cy2) * Sy2) * is;

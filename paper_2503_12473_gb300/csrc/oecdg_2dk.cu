@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
   using MD = Modes2<K, B>;
   constexpr int F = Fields2<SYS>::F, M = MD::M, N = K + 1;
   const int mesh = blockIdx.z;
+  __shared__ double isg[F];  // 1/sigma of this mesh's fields, once per block
+  oe_inv_sigma<F>(sigma, mesh, isg);
   int i, j;
   cell_of_thread(g, i, j);
   if (i >= cells_x(g, mesh) || j >= cells_y(g, mesh)) return;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
       for (int m = 0; m <= K; ++m) S[n][m] = 0.0;
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
-      const double sn = n == 0 ? 2.0 / g.hx : 2.0 / g.hy, st = n == 0 ? 2.0 / g.hy : 2.0 / g.hx;
+      const double sn = n == 0 ? g.i2x : g.i2y, st = n == 0 ? g.i2y : g.i2x;  // 2/h normal, tangential
 #pragma unroll 1
       for (int side = 0; side < 2; ++side) {
         const double s = 2.0 * side - 1.0;
@@ -500,8 +502,8 @@ __global__ void __launch_bounds__(NTK) k_oe2k(Geo g, const double* __restrict__ 
       }
     }
     if (sg != 0.0) {
-      const double is = 1.0 / sg;
-      double hx = 1.0 / g.hx, hy = 1.0 / g.hy;  // h^(m-1)
+      const double is = isg[f];
+      double hx = g.i1x, hy = g.i1y;  // h^(m-1)
 #pragma unroll
       for (int m = 0; m <= K; ++m) {
         const double c = 0.25 * (2 * m + 1) / ((2 * K - 1) * fact(m));

@@ -98,6 +98,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   g.adv_x = d.adv_x;
   g.adv_y = d.adv_y;
   g.cfl = d.cfl;
+  finish_geo(g);
   c->numel = (size_t)2 * c->F * c->M * g.plane;
   c->nblk = d.dim == 2 ? (c->gen2 ? partial_blocks_2k(g) : partial_blocks_2d(g)) : partial_blocks_1d(g);
   c->wave_blk = d.dim == 2 ? wave_blocks_2d(g) : wave_blocks_1d(g);

@@ -81,11 +81,15 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
   const int mesh = local & 1, t = local >> 1;
   const int i = (t % in.tx) * 32 + (threadIdx.x & 31);
   const int j = (t / in.tx) * R + (threadIdx.x >> 5);
+  __shared__ double isg[Fields<SYS>::F];
+  oe_inv_sigma<Fields<SYS>::F>(in.sigma, mesh, isg);
   // square cells: the isotropic variant, as the single-mesh launch chooses it
   if (in.g.hx == in.g.hy)
-    oe_cell2d<SYS, BC, false, 0, true>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
+    oe_cell2d<SYS, BC, false, 0, true>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j,
+                                       nullptr, isg);
   else
-    oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j);
+    oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j, nullptr,
+                              isg);
 }
 
 // avg and sigma per instance, mesh and field: grid (F, 2, n), one warp each,
@@ -496,6 +500,7 @@ cdg_status cdg_init_batch(const cdg_mesh_desc* descs, int n, void* stream, cdg_b
     g.adv_x = d.adv_x;
     g.adv_y = d.adv_y;
     g.cfl = d.cfl;
+    finish_geo(g);
     const size_t st = (size_t)2 * 4 * 9 * g.plane;
     const size_t tiles = (size_t)((d.nx + 31) / 32) * ((d.ny + 1) / 2);
     in.a = p; p += st;

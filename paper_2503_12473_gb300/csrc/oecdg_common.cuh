@@ -108,7 +108,14 @@ __device__ __forceinline__ double sqrt_pos(double x) {
 //             slot after its last cell; the primal mesh leaves the slot unused);
 //   plane:    nxs * nys;
 //   bcs:      per side (x-low, x-high, y-low, y-high): SIDE_PERIODIC,
-//             SIDE_TRANSMISSIVE or SIDE_REFLECTIVE (read by BC_GENERAL kernels).
+//             SIDE_TRANSMISSIVE or SIDE_REFLECTIVE (read by BC_GENERAL kernels);
+//   i1x ...:  constants of the cell size that the per-cell code of the 2D OE
+//             kernels needs, set once on the host by finish_geo, so that no
+//             thread divides (an IEEE quotient has the same bits on either
+//             side): 1/hx, 1/hy, 2/hx, 2/hy, 1/(12 hx), 1/(12 hy), 5 hx/24,
+//             5 hy/24.  (The stage kernels keep their own quotients: taken from
+//             here they left the times unchanged or slower, with more of the
+//             tiled kernel's register spills reaching DRAM.)
 struct Geo {
   int nx, ny;
   long long plane;
@@ -118,7 +125,33 @@ struct Geo {
   double cfl;
   int nxs, nys;
   int bcs[4];
+  double i1x, i1y, i2x, i2y, i12x, i12y, h24x5, h24y5;
 };
+
+// The cell-size constants of Geo, from hx and hy (the same expressions the
+// per-cell code would evaluate).
+inline void finish_geo(Geo& g) {
+  g.i1x = 1.0 / g.hx;
+  g.i1y = 1.0 / g.hy;
+  g.i2x = 2.0 / g.hx;
+  g.i2y = 2.0 / g.hy;
+  g.i12x = 1.0 / (12.0 * g.hx);
+  g.i12y = 1.0 / (12.0 * g.hy);
+  g.h24x5 = 5.0 * g.hx / 24.0;
+  g.h24y5 = 5.0 * g.hy / 24.0;
+}
+
+// 1/sigma of the F fields of `mesh` into shared isg[F] by the block's first
+// threads (the same IEEE quotient the cell code would take), then a barrier:
+// every thread of the block must call it.
+template <int F>
+__device__ __forceinline__ void oe_inv_sigma(const double* __restrict__ sigma, int mesh, double* isg) {
+  if (threadIdx.x < F) {
+    const double sg = sigma[mesh * F + threadIdx.x];
+    isg[threadIdx.x] = sg != 0.0 ? 1.0 / sg : 0.0;
+  }
+  __syncthreads();
+}
 
 // Stored cells of mesh `mesh` per direction (the dual mesh has the wall slots).
 __host__ __device__ __forceinline__ int cells_x(const Geo& g, int mesh) { return mesh == 0 ? g.nx : g.nxs; }

@@ -140,6 +140,7 @@ extern "C" cdg_status cdg_oe_damp_noalloc(const cdg_mesh_desc* desc, const doubl
   g.adv_x = d.adv_x;
   g.adv_y = d.adv_y;
   g.cfl = d.cfl;
+  finish_geo(g);
   const int sys = d.system == CDG_EULER ? SYS_EULER : SYS_ADV;
   const int bc = uniform_side_bc(d) == CDG_PERIODIC ? BC_PERIODIC : BC_TRANSMISSIVE;
 
