@@ -289,6 +289,23 @@ def random_modal(shape, seed: int, scale: float = 1.0, decay: float = 0.5, nmode
     return u * s.reshape(sh)
 
 
+def counter_uniform(shape, seed: int) -> np.ndarray:
+    """Seeded values uniform in [-1, 1) that are the same on every machine and
+    numpy version: element i is SplitMix64 (Steele, Lea and Flood, "Fast
+    splittable pseudorandom number generators", OOPSLA 2014) of the counter
+    seed * 2^32 + i, its top 53 bits read as a fraction in [0, 1), then
+    mapped by 2 x - 1 (all steps exact in integer and binary arithmetic)."""
+    n = int(np.prod(shape))
+    with np.errstate(over="ignore"):
+        z = np.arange(n, dtype=np.uint64) + np.uint64(seed) * np.uint64(1 << 32)
+        z = z + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (2.0 * u - 1.0).reshape(shape)
+
+
 def perturbation(shape, seed: int, amp: float = 1e-3):
     rng = np.random.default_rng(seed)
     return amp * rng.standard_normal(shape)
@@ -331,12 +348,12 @@ def steady_wave_2d_workload(n: int = 1024, k: int = 3, basis: int = BASIS_P) -> 
 
 
 def riemann_2d(n: int = 1024, steps: int = 200) -> Workload:
-    return Workload("euler_2d_riemann_q2_1024", 2, n, n, 2, EULER, TRANSMISSIVE, 0.0, 1.0, 0.0, 1.0, cfl=0.1,
+    return Workload(f"euler_2d_riemann_q2_{n}", 2, n, n, 2, EULER, TRANSMISSIVE, 0.0, 1.0, 0.0, 1.0, cfl=0.1,
                     steps=steps, u0=riemann_quadrants())
 
 
 def vortex_2d(n: int = 256, steps: int = 400) -> Workload:
-    return Workload("euler_2d_vortex_q2_256", 2, n, n, 2, EULER, PERIODIC, 0.0, 10.0, 0.0, 10.0, cfl=0.1,
+    return Workload(f"euler_2d_vortex_q2_{n}", 2, n, n, 2, EULER, PERIODIC, 0.0, 10.0, 0.0, 10.0, cfl=0.1,
                     steps=steps, u0=isentropic_vortex())
 
 

@@ -74,3 +74,18 @@ def test_random_modal_is_seeded_and_decays():
     assert np.array_equal(u, v)
     rms = np.sqrt((u ** 2).mean(axis=(0, 1, 3, 4)))
     assert rms[8] < rms[0] * 0.05  # mode m scaled by 0.5^m
+
+
+def test_counter_uniform_is_splitmix64():
+    """counter_uniform's element 0 for seed 0 is the first SplitMix64 output
+    from state 0, 0xE220A8397B1DCDAF (the generator's published reference
+    value), read as the fraction of its top 53 bits and mapped to [-1, 1);
+    values are in range, seeds differ, and the mean and spread are uniform's."""
+    from paper_2503_12473_gb300 import workloads as W
+    top53 = 0xE220A8397B1DCDAF >> 11
+    assert W.counter_uniform((1,), 0)[0] == 2.0 * (top53 / 2.0 ** 53) - 1.0
+    a = W.counter_uniform((200000,), 7)
+    assert a.min() >= -1.0 and a.max() < 1.0
+    assert abs(a.mean()) < 0.01 and abs(a.std() - 1 / np.sqrt(3)) < 0.01
+    assert not np.array_equal(W.counter_uniform((64,), 1), W.counter_uniform((64,), 2))
+    np.testing.assert_array_equal(W.counter_uniform((4, 16), 3).ravel(), W.counter_uniform((64,), 3))
