@@ -513,9 +513,11 @@ template <int SYS, bool ISO>
 __global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                                  const double* __restrict__ dt, const double* __restrict__ sigma,
                                                  int* __restrict__ status, double* __restrict__ rec) {
+  __shared__ double isg[Fields<SYS>::F];
+  oe_inv_sigma<Fields<SYS>::F>(sigma, blockIdx.z, isg);
   oe_cell2d<SYS, BC_PERIODIC, false, 1, ISO>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
                                          blockIdx.x * 32 + (threadIdx.x & 31),
-                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec);
+                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec, isg);
 }
 
 // Reverse of one derivative order M of the face sums of one field: given the
@@ -528,7 +530,7 @@ __device__ __forceinline__ void oe_order_vjp(const Geo& g, const double* u, cons
                                              const int* oi, const int* oj, double Sbx, double Sby, double* ub,
                                              double (&wb)[4][9]) {
   const long long P = g.plane;
-  const double dx1 = 2.0 / g.hx, dy1 = 2.0 / g.hy;
+  const double dx1 = g.i2x, dy1 = g.i2y;  // 2/hx, 2/hy
 #pragma unroll
   for (int n = 0; n < 2; ++n) {
     const double Sb = n == 0 ? Sbx : Sby;
@@ -705,8 +707,8 @@ __global__ void __launch_bounds__(AT) k_oe_vjp2d(Geo g, const double* __restrict
   for (int f = 0; f < F; ++f) w0[f] = uh[self + f * 9 * P];
   double bx, by, gbx[4], gby[4];
   beta_and_grad<SYS>(g, w0, bx, by, gbx, gby);
-  const double cx[3] = {1.0 / (12.0 * g.hx), 0.25, 5.0 * g.hx / 24.0};
-  const double cy[3] = {1.0 / (12.0 * g.hy), 0.25, 5.0 * g.hy / 24.0};
+  const double cx[3] = {g.i12x, 0.25, g.h24x5};  // 1/(12 hx), 1/4, 5 hx/24
+  const double cy[3] = {g.i12y, 0.25, g.h24y5};
 
   // the forward's delta^m, the field of the max and its face sums
   const double* r = rec + ((long long)mesh * P + (long long)jc * g.nx + ic) * 12;

@@ -194,6 +194,7 @@ struct BPersistArgs {
 template <int SYS, int BC, int R>
 __global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
   constexpr int F = Fields<SYS>::F;
+  __shared__ double isg[F];  // 1/sigma of the OE phase's current tile (its instance and mesh)
   const long long nwave = (long long)a.n * WB;
   for (int s = 0; s < a.nsteps; ++s) {
     for (long long it = blockIdx.x; it < nwave; it += gridDim.x)
@@ -230,11 +231,14 @@ __global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
         const int mesh = local & 1, t = local >> 1;
         const int i = (t % in.tx) * 32 + (threadIdx.x & 31), j = (t / in.tx) * R + (threadIdx.x >> 5);
         double* out = l == 2 ? in.u : in.b;
+        __syncthreads();  // the previous tile's readers of isg are done
+        oe_inv_sigma<F>(in.sigma, mesh, isg);
         if (in.g.hx == in.g.hy)
-          oe_cell2d<SYS, BC, false, 0, true, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i, j);
+          oe_cell2d<SYS, BC, false, 0, true, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i, j,
+                                                    nullptr, isg);
         else
           oe_cell2d<SYS, BC, false, 0, false, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i,
-                                                     j);
+                                                     j, nullptr, isg);
       }
       if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
     }

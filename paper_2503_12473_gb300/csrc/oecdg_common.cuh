@@ -143,11 +143,12 @@ inline void finish_geo(Geo& g) {
 
 // 1/sigma of the F fields of `mesh` into shared isg[F] by the block's first
 // threads (the same IEEE quotient the cell code would take), then a barrier:
-// every thread of the block must call it.
+// every thread of the block must call it.  The load goes to L2 (ld.global.cg),
+// so a persistent kernel may call it on sigma written earlier in the launch.
 template <int F>
-__device__ __forceinline__ void oe_inv_sigma(const double* __restrict__ sigma, int mesh, double* isg) {
+__device__ __forceinline__ void oe_inv_sigma(const double* sigma, int mesh, double* isg) {
   if (threadIdx.x < F) {
-    const double sg = sigma[mesh * F + threadIdx.x];
+    const double sg = __ldcg(sigma + mesh * F + threadIdx.x);
     isg[threadIdx.x] = sg != 0.0 ? 1.0 / sg : 0.0;
   }
   __syncthreads();
