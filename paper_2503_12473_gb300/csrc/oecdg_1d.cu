@@ -32,14 +32,15 @@ struct Fields1 {
 template <int SYS>
 __device__ __forceinline__ void flux1(const Geo& g, const double* w, double* f) {
   if (SYS == SYS_EULER) {
-    const double r = __drcp_rn(w[0]);
+    const double r = rcp_pos(w[0]);  // seeded reciprocal, within 1 ulp (oecdg_common.cuh)
     const double v = w[1] * r;
     // multiply-adds written out as fma: every kernel that inlines this rounds
     // alike (the compiler's own contraction may differ between them)
-    const double p = (g.gamma - 1.0) * fma(-0.5 * w[1], v, w[2]);
+    const double e = fma(-0.5 * w[1], v, w[2]);  // E - kinetic energy
+    const double p = (g.gamma - 1.0) * e;
     f[0] = w[1];
     f[1] = fma(w[1], v, p);
-    f[2] = (w[2] + p) * v;
+    f[2] = fma(g.gamma - 1.0, e, w[2]) * v;  // (E + p) v, E + p as one fma
   } else if (SYS == SYS_BURGERS) {
     f[0] = 0.5 * w[0] * w[0];
   } else {
@@ -47,14 +48,16 @@ __device__ __forceinline__ void flux1(const Geo& g, const double* w, double* f) 
   }
 }
 
-// Wave speed |f'(w)| (Euler: |v| + c); -1 for a non-physical Euler state.
+// Wave speed |f'(w)| (Euler: |v| + c, with the seeded reciprocal and square
+// root as in the 2D kernels); -1 for a non-physical Euler state.
 template <int SYS>
 __device__ __forceinline__ double speed1(const Geo& g, const double* w) {
   if (SYS == SYS_EULER) {
-    const double v = w[1] / w[0];
+    const double r = rcp_pos(w[0]);  // NaN for rho <= 0 or subnormal: flagged below
+    const double v = w[1] * r;
     const double p = (g.gamma - 1.0) * fma(-0.5 * w[1], v, w[2]);
     if (!(w[0] > 0.0 && p > 0.0)) return -1.0;
-    return fabs(v) + sqrt(g.gamma * p / w[0]);
+    return fabs(v) + sqrt_pos(fma(g.gamma * p, r, SQ_FLOOR));
   } else if (SYS == SYS_BURGERS) {
     return fabs(w[0]);
   }
@@ -63,76 +66,116 @@ __device__ __forceinline__ double speed1(const Geo& g, const double* w) {
 
 // L_a = (2a+1) [ sum_{s,q} (w_q/4)(w/tau_max) P_a(xi) + (1/h) sum (w_q/2) f(w) P_a'(xi)
 //               - (1/h)(f_R - (-1)^a f_L) ] - u_a / tau_max
+// in two parts.  rhs1d_half: the sums over the K+1 Gauss points of half sx of
+// cell i (the overlapping cell there is smooth) and the flux at that half's
+// face (sx = 0: the left end, sx = 1: the right end), from zero.  The cell's
+// sums are half 0's plus half 1's, one addition per coefficient, so a cell
+// computed by one thread and a cell split over two lanes (one half each) get
+// the same bits.
 template <int SYS, int BC, int K, int LD = LD_NC>
-__device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restrict__ u, int mesh, int i, double inv_tm,
-                                           double (&L)[Fields1<SYS>::F][K + 1]) {
+__device__ __forceinline__ void rhs1d_half(const Geo& g, const double* __restrict__ u, int mesh, int i, int sx,
+                                           double (&Ad)[Fields1<SYS>::F][K + 1], double (&Bd)[Fields1<SYS>::F][K + 1],
+                                           double (&fS)[Fields1<SYS>::F]) {
   constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
   const long long P = g.plane;
   const double* uo = u + (long long)(1 - mesh) * F * M * P;
-  const double* us = u + (long long)mesh * F * M * P + i;
   const int off = mesh == 0 ? -1 : 0;
-  double Ad[F][M], Bd[F][M];  // dissipation and flux-gradient sums
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
     for (int a = 0; a < M; ++a) Ad[f][a] = Bd[f][a] = 0.0;
-  double fL[F], fR[F];
-#pragma unroll
-  for (int sx = 0; sx < 2; ++sx) {
-    bool mir = false;
-    const int oi = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, unwrapped(g, 0, mesh, i) + sx + off, mir)
-                                    : wrap_index<BC>(i + sx + off, g.nx);
-    const double* c = uo + oi;
-    double w[F][M];
-#pragma unroll
-    for (int f = 0; f < F; ++f)
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
-        w[f][a] = ldv<LD>(c + (f * M + a) * P);
-        if (BC == BC_GENERAL && mir) w[f][a] = apply_sign(w[f][a], mirror_sign(true, false, SYS == SYS_EULER, f, a, 0));
-      }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      const double xo = xo1(N, sx, q), xsf = xs1(N, sx, q);
-      double V[F], fl[F];
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-        double v = w[f][0];
-#pragma unroll
-        for (int a = 1; a < M; ++a) v = fma(lpd(a, 0, xo), w[f][a], v);
-        V[f] = v;
-      }
-      flux1<SYS>(g, V, fl);
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-          Ad[f][a] = fma(gw1(N, q) * lpd(a, 0, xsf), V[f], Ad[f][a]);
-          if (a > 0) Bd[f][a] = fma(gw1(N, q) * lpd(a, 1, xsf), fl[f], Bd[f][a]);
-        }
-      }
-    }
-    // face of this half: the overlapping cell's centre (xi' = 0)
-    double V[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-      double v = w[f][0];
-#pragma unroll
-      for (int a = 2; a < M; a += 2) v = fma(lpd(a, 0, 0.0), w[f][a], v);
-      V[f] = v;
-    }
-    if (sx) flux1<SYS>(g, V, fR);
-    else flux1<SYS>(g, V, fL);
-  }
-  const double ih = 1.0 / g.hx;
+  bool mir = false;
+  const int oi = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, unwrapped(g, 0, mesh, i) + sx + off, mir)
+                                  : wrap_index<BC>(i + sx + off, g.nx);
+  const double* c = uo + oi;
+  double w[F][M];
 #pragma unroll
   for (int f = 0; f < F; ++f)
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      const double face = fR[f] - ((a & 1) ? -fL[f] : fL[f]);
+      w[f][a] = ldv<LD>(c + (f * M + a) * P);
+      if (BC == BC_GENERAL && mir) w[f][a] = apply_sign(w[f][a], mirror_sign(true, false, SYS == SYS_EULER, f, a, 0));
+    }
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    // the half's point constants (sx is a run-time value in the split kernels:
+    // each constant is folded for both halves and chosen by a select, so no
+    // FP64 work is added and both kernels use the same values)
+    double po[M], pa[M], pb[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      po[a] = sx ? lpd(a, 0, xo1(N, 1, q)) : lpd(a, 0, xo1(N, 0, q));
+      pa[a] = sx ? gw1(N, q) * lpd(a, 0, xs1(N, 1, q)) : gw1(N, q) * lpd(a, 0, xs1(N, 0, q));
+      pb[a] = sx ? gw1(N, q) * lpd(a, 1, xs1(N, 1, q)) : gw1(N, q) * lpd(a, 1, xs1(N, 0, q));
+    }
+    double V[F], fl[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      double v = w[f][0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) v = fma(po[a], w[f][a], v);
+      V[f] = v;
+    }
+    flux1<SYS>(g, V, fl);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        Ad[f][a] = fma(pa[a], V[f], Ad[f][a]);
+        if (a > 0) Bd[f][a] = fma(pb[a], fl[f], Bd[f][a]);
+      }
+    }
+  }
+  // face of this half: the overlapping cell's centre (xi' = 0)
+  double V[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    double v = w[f][0];
+#pragma unroll
+    for (int a = 2; a < M; a += 2) v = fma(lpd(a, 0, 0.0), w[f][a], v);
+    V[f] = v;
+  }
+  flux1<SYS>(g, V, fS);
+}
+
+// L from the cell's sums (Ad, Bd: both halves added) and its face fluxes.
+template <int SYS, int K, int LD = LD_NC>
+__device__ __forceinline__ void rhs1d_finish(const Geo& g, const double* __restrict__ us, double inv_tm,
+                                             const double (&Ad)[Fields1<SYS>::F][K + 1],
+                                             const double (&Bd)[Fields1<SYS>::F][K + 1], const double* fL,
+                                             const double* fR, double (&L)[Fields1<SYS>::F][K + 1]) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
+  const long long P = g.plane;
+  const double ih = g.i1x;  // 1/h from the host
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      // an explicit add: f_R can be a product (the Euler energy flux) that the
+      // compiler would fuse into the subtraction in some kernels and not in
+      // others (where it arrives by shuffle)
+      const double face = (a & 1) ? __dadd_rn(fR[f], fL[f]) : __dsub_rn(fR[f], fL[f]);
       const double br = fma(0.25 * inv_tm, Ad[f][a], ih * fma(0.5, Bd[f][a], -face));
       L[f][a] = fma((double)(2 * a + 1), br, -inv_tm * ldv<LD>(us + (f * M + a) * P));
     }
+}
+
+// The whole cell by one thread: both halves, added.
+template <int SYS, int BC, int K, int LD = LD_NC>
+__device__ __forceinline__ void cell_rhs1d(const Geo& g, const double* __restrict__ u, int mesh, int i, double inv_tm,
+                                           double (&L)[Fields1<SYS>::F][K + 1]) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
+  double A0[F][M], B0[F][M], A1[F][M], B1[F][M], fL[F], fR[F];
+  rhs1d_half<SYS, BC, K, LD>(g, u, mesh, i, 0, A0, B0, fL);
+  rhs1d_half<SYS, BC, K, LD>(g, u, mesh, i, 1, A1, B1, fR);
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      A0[f][a] += A1[f][a];
+      B0[f][a] += B1[f][a];
+    }
+  rhs1d_finish<SYS, K, LD>(g, u + (long long)mesh * F * M * g.plane + i, inv_tm, A0, B0, fL, fR, L);
 }
 
 enum { MODE1_RHS = 0, MODE1_STAGE = 1 };
@@ -213,6 +256,121 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
                                  mesh, blockIdx.x * NT1 + threadIdx.x);
 }
 
+// The same stage with two lanes per cell (lanes 2c and 2c + 1 of a block of
+// 2 NT1 threads take cell blockIdx.x * NT1 + c): lane sx sums half sx and the
+// flux at its face, the pair swaps its sums by shuffle and adds them in the
+// one-thread order, and both lanes finish the cell alike; lane sx stores the
+// modes a with a % 2 == sx.  A 1D mesh of a few thousand cells gives each SM's
+// FP64 pipe one warp or less, so the time of a phase is that of its longest
+// warp: half the quadrature per lane shortens it.  The sigma partials of
+// lane 0 are laid out as the one-thread block's threads (cell c in thread c)
+// before the block reduction, so the partials, and hence sigma, are bit for
+// bit those of the one-thread kernel.
+template <int SYS, int BC, int K, int MODE, int LD = LD_NC>
+__device__ __forceinline__ void stage_cell1d_2l(const Geo& g, const double* __restrict__ uin, const StageComb& cb,
+                                                double* __restrict__ out, const double* __restrict__ dt,
+                                                double* __restrict__ pblk, int mesh, int i, int sx) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1, N = K + 1;
+  const unsigned full = 0xffffffffu;
+  const bool active = i < cells_x(g, mesh);
+  const int ic = active ? i : 0;
+  const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
+  const double inv_tm = 1.0 / tm;
+  double A[F][M], B[F][M], fS[F], fO[F];
+  rhs1d_half<SYS, BC, K, LD>(g, uin, mesh, ic, sx, A, B, fS);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const double oa = __shfl_xor_sync(full, A[f][a], 1), ob = __shfl_xor_sync(full, B[f][a], 1);
+      A[f][a] = sx ? oa + A[f][a] : A[f][a] + oa;  // half 0 + half 1
+      B[f][a] = sx ? ob + B[f][a] : B[f][a] + ob;
+    }
+    fO[f] = __shfl_xor_sync(full, fS[f], 1);
+  }
+  double fL[F], fR[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    fL[f] = sx ? fO[f] : fS[f];
+    fR[f] = sx ? fS[f] : fO[f];
+  }
+  const long long P = g.plane;
+  const long long base = (long long)mesh * F * M * P + ic;
+  double L[F][M];
+  rhs1d_finish<SYS, K, LD>(g, uin + base, inv_tm, A, B, fL, fR, L);
+  if (MODE == MODE1_RHS) {
+    if (active)
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+          if ((a & 1) == sx) out[base + (f * M + a) * P] = L[f][a];
+    return;
+  } else {
+    __shared__ double sh[96];
+    __shared__ double cell[3][NT1];  // one field's (sum, max, min) per cell
+    const double tl = cb.ct * tau;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      double v[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        const long long id = base + (f * M + a) * P;
+        double s = tl * L[f][a];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m < cb.n) s = fma(cb.c[m], ldv<LD>(cb.u[m] + id), s);
+        v[a] = s;
+        if (active && (a & 1) == sx) out[id] = s;
+      }
+      double mx = -DINF1, mn = DINF1;
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        double val = v[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) val = fma(lpd(a, 0, gn1(N, q)), v[a], val);
+        mx = fmax(mx, val);
+        mn = fmin(mn, val);
+      }
+      double s = active ? v[0] : 0.0;
+      if (BC == BC_GENERAL) s *= cell_weight(g, mesh, ic, 0, 1);  // a wall-centred dual cell counts half
+      if (!active) {
+        mx = -DINF1;
+        mn = DINF1;
+      }
+      if (sx == 0) {
+        const int c = threadIdx.x >> 1;
+        cell[0][c] = s;
+        cell[1][c] = mx;
+        cell[2][c] = mn;
+      }
+      __syncthreads();
+      const int t = threadIdx.x;
+      s = t < NT1 ? cell[0][t] : 0.0;
+      mx = t < NT1 ? cell[1][t] : -DINF1;
+      mn = t < NT1 ? cell[2][t] : DINF1;
+      block_reduce3(s, mx, mn, sh);  // its barriers also free cell[] for the next field
+      if (threadIdx.x == 0) {
+        double* p = pblk + f * 3;
+        p[0] = s;
+        p[1] = mx;
+        p[2] = mn;
+      }
+    }
+  }
+}
+
+template <int SYS, int BC, int K, int MODE>
+__global__ void __launch_bounds__(2 * NT1) k_stage1d_2l(Geo g, const double* __restrict__ uin, StageComb cb,
+                                                        double* __restrict__ out, const double* __restrict__ dt,
+                                                        double* __restrict__ partials) {
+  constexpr int F = Fields1<SYS>::F;
+  const int mesh = blockIdx.y;
+  stage_cell1d_2l<SYS, BC, K, MODE>(g, uin, cb, out, dt,
+                                    partials + (mesh * (long long)gridDim.x + blockIdx.x) * F * 3, mesh,
+                                    blockIdx.x * NT1 + (threadIdx.x >> 1), threadIdx.x & 1);
+}
+
 // delta^m = (2m+1) h^{m-1} / ((2K-1) m!) beta (|d^m (u^C-u^D)|_R + |...|_L) / sigma
 // for m = 0..K, max over fields; then the exact damping of mode a by
 // exp(-tau sum_{m <= a} delta^m).  The face points are the cell ends xi = +-1,
@@ -220,7 +378,8 @@ __global__ void __launch_bounds__(NT1) k_stage1d(Geo g, const double* __restrict
 template <int SYS, int BC, int K, bool WRITE_DELTA, int LD = LD_NC>
 __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
-                                          double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i) {
+                                          double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
+                                          const double* __restrict__ isg = nullptr) {
   constexpr int F = Fields1<SYS>::F, M = K + 1;
   if (i >= cells_x(g, mesh)) return;
   const long long P = g.plane;
@@ -239,13 +398,13 @@ __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict
     atomicOr(status, ST_NONPHYSICAL);
     beta = 0.0;
   }
-  const double h = g.hx, d1 = 2.0 / h;
+  const double h = g.hx, d1 = g.i2x;  // 2/h from the host
   double km[M];  // (2m+1) h^{m-1} / ((2K-1) m!) (2/h)^m
   {
-    double hp = 1.0 / h, dp = 1.0;
+    double hp = g.i1x, dp = 1.0;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      km[m] = (2 * m + 1) * hp * dp / ((2 * K - 1) * fact(m));
+      km[m] = (2 * m + 1) * hp * dp * (1.0 / ((2 * K - 1) * fact(m)));
       hp *= h;
       dp *= d1;
     }
@@ -268,7 +427,7 @@ __device__ __forceinline__ void oe_cell1d(const Geo& g, const double* __restrict
       }
     }
     if (sg != 0.0) {
-      const double is = beta / sg;
+      const double is = isg ? beta * isg[f] : beta / sg;
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         // reference-coordinate m-th derivatives: own trace at xi = +-1, other at 0
@@ -313,8 +472,117 @@ template <int SYS, int BC, int K, bool WRITE_DELTA>
 __global__ void __launch_bounds__(NT1) k_oe1d(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
                                               const double* __restrict__ dt, const double* __restrict__ sigma,
                                               double* __restrict__ delta_out, int* __restrict__ status) {
+  __shared__ double isg[Fields1<SYS>::F];  // 1/sigma of this mesh's fields, once per block
+  oe_inv_sigma<Fields1<SYS>::F>(sigma, blockIdx.y, isg);
   oe_cell1d<SYS, BC, K, WRITE_DELTA>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.y,
-                                     blockIdx.x * NT1 + threadIdx.x);
+                                     blockIdx.x * NT1 + threadIdx.x, isg);
+}
+
+// The OE step with two lanes per cell (the layout of k_stage1d_2l): lane sx
+// forms the jumps at its cell end (sx = 0: the left end, against the left
+// overlapping cell; 1: the right end), the pair swaps them, and both lanes
+// take delta^m exactly as oe_cell1d does; lane sx evaluates the decay factors
+// of, and stores, the modes a with a % 2 == sx.  Bit for bit oe_cell1d's
+// result.
+template <int SYS, int BC, int K, bool WRITE_DELTA>
+__device__ __forceinline__ void oe_cell1d_2l(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
+                                             const double* __restrict__ dt, const double* __restrict__ sigma,
+                                             double* __restrict__ delta_out, int* __restrict__ status, int mesh,
+                                             int i, int sx, const double* __restrict__ isg) {
+  constexpr int F = Fields1<SYS>::F, M = K + 1;
+  const unsigned full = 0xffffffffu;
+  const bool active = i < cells_x(g, mesh);  // no early return: the pair shuffles
+  const int ic = active ? i : 0;
+  const long long P = g.plane;
+  const double* us = uh + (long long)mesh * F * M * P + ic;
+  const double* uo = uh + (long long)(1 - mesh) * F * M * P;
+  const int off = mesh == 0 ? -1 : 0;
+  bool mir = false;
+  const int iu = BC == BC_GENERAL ? unwrapped(g, 0, mesh, ic) : ic;
+  const int on = BC == BC_GENERAL ? side_index(g, 0, 1 - mesh, iu + sx + off, mir)
+                                  : wrap_index<BC>(ic + sx + off, g.nx);
+  double wa[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) wa[f] = __ldg(us + (f * M) * P);
+  double beta = speed1<SYS>(g, wa);
+  if (beta < 0.0) {
+    if (active && sx == 0) atomicOr(status, ST_NONPHYSICAL);
+    beta = 0.0;
+  }
+  const double h = g.hx, d1 = g.i2x;
+  double km[M];
+  {
+    double hp = g.i1x, dp = 1.0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      km[m] = (2 * m + 1) * hp * dp * (1.0 / ((2 * K - 1) * fact(m)));
+      hp *= h;
+      dp *= d1;
+    }
+  }
+  double dl[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) dl[m] = 0.0;
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const double sg = __ldg(sigma + mesh * F + f);
+    double u[M], nb[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      u[a] = __ldg(us + (f * M + a) * P);
+      nb[a] = __ldg(uo + (f * M + a) * P + on);
+      if (BC == BC_GENERAL) nb[a] = apply_sign(nb[a], mirror_sign(mir, false, SYS == SYS_EULER, f, a, 0));
+    }
+    const double is = beta * isg[f];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      // this lane's end: own trace at xi = -1 (sx = 0) or +1, the other cell at 0
+      double j = 0.0;
+#pragma unroll
+      for (int a = m; a < M; ++a) {
+        const double o = lpd(a, m, 0.0);
+        j = fma(sx ? lpd(a, m, 1.0) : lpd(a, m, -1.0), u[a], j);
+        j = fma(-o, nb[a], j);
+      }
+      const double jo = __shfl_xor_sync(full, j, 1);
+      const double jr = sx ? j : jo, jl = sx ? jo : j;
+      if (sg != 0.0) dl[m] = fmax(dl[m], km[m] * (fabs(jr) + fabs(jl)) * is);
+    }
+  }
+  if (!active) return;
+  if (WRITE_DELTA && sx == 0) {
+    double* dp = delta_out + ((long long)mesh * g.nxs + ic) * M;
+#pragma unroll
+    for (int m = 0; m < M; ++m) dp[m] = dl[m];
+  }
+  if (usig != nullptr) {
+    const double tau = __ldg(dt);
+    double e[M];
+    double rate = dl[0];
+    e[0] = 1.0;
+#pragma unroll
+    for (int a = 1; a < M; ++a) {
+      rate += dl[a];
+      e[a] = (a & 1) == sx ? exp(-tau * rate) : 0.0;
+    }
+    double* os = usig + (long long)mesh * F * M * P + ic;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+        if ((a & 1) == sx) os[(f * M + a) * P] = a == 0 ? __ldg(us + (f * M) * P) : __ldg(us + (f * M + a) * P) * e[a];
+    }
+  }
+}
+
+template <int SYS, int BC, int K, bool WRITE_DELTA>
+__global__ void __launch_bounds__(2 * NT1) k_oe1d_2l(Geo g, const double* __restrict__ uh, double* __restrict__ usig,
+                                                     const double* __restrict__ dt, const double* __restrict__ sigma,
+                                                     double* __restrict__ delta_out, int* __restrict__ status) {
+  __shared__ double isg[Fields1<SYS>::F];  // 1/sigma of this mesh's fields, once per block
+  oe_inv_sigma<Fields1<SYS>::F>(sigma, blockIdx.y, isg);
+  oe_cell1d_2l<SYS, BC, K, WRITE_DELTA>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.y,
+                                        blockIdx.x * NT1 + (threadIdx.x >> 1), threadIdx.x & 1, isg);
 }
 
 template <int SYS, int K>
@@ -450,6 +718,7 @@ template <int SYS, int BC, int K>
 __global__ void __launch_bounds__(NT1) k_persist1d(Geo g, Persist1 a) {
   constexpr int F = Fields1<SYS>::F, M = K + 1;
   __shared__ double sh[32];
+  __shared__ double isg[F];  // 1/sigma of the OE phase's current tile (its mesh)
   const long long ntiles = 2 * a.nblk;
   persist_wave1d<SYS, K>(g, a, a.uin[0], sh);
   if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
@@ -468,9 +737,12 @@ __global__ void __launch_bounds__(NT1) k_persist1d(Geo g, Persist1 a) {
       }
       if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
       if (a.oe) {
-        for (long long b = blockIdx.x; b < ntiles; b += gridDim.x)
+        for (long long b = blockIdx.x; b < ntiles; b += gridDim.x) {
+          __syncthreads();  // the previous tile's readers of isg are done
+          oe_inv_sigma<F>(a.sigma, (int)(b & 1), isg);
           oe_cell1d<SYS, BC, K, false, LD_CA>(g, a.ua, a.dst[l], a.dt, a.sigma, nullptr, a.status, (int)(b & 1),
-                                              (int)((b >> 1) * NT1) + threadIdx.x);
+                                              (int)((b >> 1) * NT1) + threadIdx.x, isg);
+        }
       } else {
         const long long n = 2LL * F * M * g.plane;
         for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -512,11 +784,11 @@ long long partial_blocks_1d(const Geo& g) { return (g.nxs + NT1 - 1) / NT1; }
 
 cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, const double* uin,
                            const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st) {
-  const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);
+  const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);  // NT1 cells per block, two lanes each
   by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
     constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
-    if (rhs_only) k_stage1d<S_, B_, K_, MODE1_RHS><<<grid, NT1, 0, st>>>(g, uin, cb, out, dt, partials);
-    else k_stage1d<S_, B_, K_, MODE1_STAGE><<<grid, NT1, 0, st>>>(g, uin, cb, out, dt, partials);
+    if (rhs_only) k_stage1d_2l<S_, B_, K_, MODE1_RHS><<<grid, 2 * NT1, 0, st>>>(g, uin, cb, out, dt, partials);
+    else k_stage1d_2l<S_, B_, K_, MODE1_STAGE><<<grid, 2 * NT1, 0, st>>>(g, uin, cb, out, dt, partials);
   });
   return cudaGetLastError();
 }
@@ -526,8 +798,8 @@ cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, 
   const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);
   by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
     constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
-    if (delta) k_oe1d<S_, B_, K_, true><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
-    else k_oe1d<S_, B_, K_, false><<<grid, NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+    if (delta) k_oe1d_2l<S_, B_, K_, true><<<grid, 2 * NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
+    else k_oe1d_2l<S_, B_, K_, false><<<grid, 2 * NT1, 0, st>>>(g, uh, usig, dt, sigma, delta, status);
   });
   return cudaGetLastError();
 }

@@ -212,15 +212,17 @@ __host__ __device__ __forceinline__ double cell_weight(const Geo& g, int mesh, i
 }
 
 // 2D Euler flux components at a conserved state (rho, mx, my, E).  Every
-// multiply-add is an explicit fma: the compiler's own contraction may differ
-// between the kernels that inline these (single-mesh, batched, persistent,
-// recording), whose results must agree bit for bit.
+// multiply-add is an explicit fma, E + p included (written as one, not left to
+// the compiler): its own contraction may differ between the kernels that
+// inline these (single-mesh, batched, persistent, recording), whose results
+// must agree bit for bit.
 struct Euler2 {
   __device__ static __forceinline__ void both(const double* w, double g, double* f1, double* f2) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
-    const double H = w[3] + p;
+    const double e = fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);  // E - kinetic energy
+    const double p = (g - 1.0) * e;
+    const double H = fma(g - 1.0, e, w[3]);  // E + p, one rounding
     f1[0] = w[1];
     f1[1] = fma(w[1], vx, p);
     f1[2] = w[2] * vx;
@@ -233,20 +235,22 @@ struct Euler2 {
   __device__ static __forceinline__ void fx(const double* w, double g, double* f1) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
+    const double e = fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
+    const double p = (g - 1.0) * e;
     f1[0] = w[1];
     f1[1] = fma(w[1], vx, p);
     f1[2] = w[2] * vx;
-    f1[3] = (w[3] + p) * vx;
+    f1[3] = fma(g - 1.0, e, w[3]) * vx;
   }
   __device__ static __forceinline__ void fy(const double* w, double g, double* f2) {
     const double r = rcp_pos(w[0]);
     const double vx = w[1] * r, vy = w[2] * r;
-    const double p = (g - 1.0) * fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
+    const double e = fma(-0.5, fma(w[1], vx, w[2] * vy), w[3]);
+    const double p = (g - 1.0) * e;
     f2[0] = w[2];
     f2[1] = w[1] * vy;
     f2[2] = fma(w[2], vy, p);
-    f2[3] = (w[3] + p) * vy;
+    f2[3] = fma(g - 1.0, e, w[3]) * vy;
   }
 };
 
