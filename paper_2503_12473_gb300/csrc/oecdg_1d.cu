@@ -525,7 +525,7 @@ __device__ __forceinline__ void oe_cell1d_2l(const Geo& g, const double* __restr
   for (int m = 0; m < M; ++m) dl[m] = 0.0;
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    const double sg = __ldg(sigma + mesh * F + f);
+    const double sg = sigma[mesh * F + f];  // global or shared
     double u[M], nb[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
@@ -585,8 +585,41 @@ __global__ void __launch_bounds__(2 * NT1) k_oe1d_2l(Geo g, const double* __rest
                                         blockIdx.x * NT1 + (threadIdx.x >> 1), threadIdx.x & 1, isg);
 }
 
+// The OE step of a step's stage with sigma taken in the same launch: warp f
+// of every block folds the stage kernel's block partials for (its mesh, field
+// f) in warp_sigma's fixed order (the order of k_sigma, so sigma is the same
+// bits), into shared memory; block 0 of each mesh also stores sigma and avg
+// for the context.  One launch instead of two per stage: a 1D stage is a few
+// microseconds of work, and a launch costs about as much.
+template <int SYS, int BC, int K, bool WRITE_DELTA>
+__global__ void __launch_bounds__(2 * NT1) k_oe1d_2l_sig(Geo g, const double* __restrict__ uh,
+                                                         double* __restrict__ usig, const double* __restrict__ dt,
+                                                         const double* __restrict__ partials, long long nblk,
+                                                         SigmaNorm sn, double* __restrict__ sigma,
+                                                         double* __restrict__ avg, double* __restrict__ delta_out,
+                                                         int* __restrict__ status) {
+  constexpr int F = Fields1<SYS>::F;
+  __shared__ double s_sig[2 * F], s_avg[2 * F], isg[F];
+  const int mesh = blockIdx.y, w = threadIdx.x >> 5;
+  if (w < F) warp_sigma<LD_NC>(partials, nblk, F, mesh, w, sn, s_avg, s_sig);
+  __syncthreads();
+  if (threadIdx.x < F) {
+    const double sg = s_sig[mesh * F + threadIdx.x];
+    isg[threadIdx.x] = sg != 0.0 ? 1.0 / sg : 0.0;
+    if (blockIdx.x == 0) {
+      sigma[mesh * F + threadIdx.x] = sg;
+      avg[mesh * F + threadIdx.x] = s_avg[mesh * F + threadIdx.x];
+    }
+  }
+  __syncthreads();
+  oe_cell1d_2l<SYS, BC, K, WRITE_DELTA>(g, uh, usig, dt, s_sig, delta_out, status, mesh,
+                                        blockIdx.x * NT1 + (threadIdx.x >> 1), threadIdx.x & 1, isg);
+}
+
 template <int SYS, int K>
-__global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict__ partial, int* __restrict__ status) {
+__global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict__ partial,
+                         unsigned long long* __restrict__ ticket, double T_end, double* __restrict__ dt,
+                         double* __restrict__ time, int* __restrict__ status) {
   constexpr int F = Fields1<SYS>::F, M = K + 1;
   __shared__ double sh[32];
   const long long n = 2 * g.plane;
@@ -607,6 +640,16 @@ __global__ void k_wave1d(Geo g, const double* __restrict__ u, double* __restrict
   if (threadIdx.x == 0) {
     partial[blockIdx.x * 2] = mx;
     partial[blockIdx.x * 2 + 1] = 0.0;
+  }
+  // the last block to finish (ticket: a monotone counter, zero when the
+  // context was made) folds the partials (the maximum is exact in any order)
+  // and sets tau, tau_max and the time: one launch for the time step
+  if (last_block(ticket)) {
+    double bx = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) bx = fmax(bx, __ldcg(partial + 2 * b));
+    __syncthreads();  // sh is reused
+    bx = block_reduce_max(bx, sh);
+    if (threadIdx.x == 0) finish_dt(bx, 0.0, g.hx, g.hy, 1, g.cfl, T_end, dt, time);
   }
 }
 
@@ -804,6 +847,22 @@ cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_oe1d_sig(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
+                            const double* partials, long long nblk, const SigmaNorm& sn, double* sigma, double* avg,
+                            double* delta, int* status, cudaStream_t st) {
+  const dim3 grid((g.nxs + NT1 - 1) / NT1, 2);
+  by_sys_bc_k(sys, bc, k, [&](auto S, auto B, auto Kc) {
+    constexpr int S_ = decltype(S)::value, B_ = decltype(B)::value, K_ = decltype(Kc)::value;
+    if (delta)
+      k_oe1d_2l_sig<S_, B_, K_, true><<<grid, 2 * NT1, 0, st>>>(g, uh, usig, dt, partials, nblk, sn, sigma, avg, delta,
+                                                               status);
+    else
+      k_oe1d_2l_sig<S_, B_, K_, false><<<grid, 2 * NT1, 0, st>>>(g, uh, usig, dt, partials, nblk, sn, sigma, avg,
+                                                                delta, status);
+  });
+  return cudaGetLastError();
+}
+
 int wave_blocks_1d(const Geo& g) {
   long long b = (2 * g.plane + 255) / 256;
   return (int)(b < 1184 ? b : 1184);
@@ -811,12 +870,13 @@ int wave_blocks_1d(const Geo& g) {
 
 cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* partial, int nblk, double T_end,
                         double* dt, double* time, int* status, cudaStream_t st) {
+  // partial holds nblk pairs and, after them, the ticket counter of the last block
+  unsigned long long* ticket = (unsigned long long*)(partial + 2 * (long long)nblk);
   by_sys_bc_k(sys, BC_PERIODIC, k, [&](auto S, auto, auto Kc) {
-    k_wave1d<decltype(S)::value, decltype(Kc)::value><<<nblk, 256, 0, st>>>(g, u, partial, status);
+    k_wave1d<decltype(S)::value, decltype(Kc)::value><<<nblk, 256, 0, st>>>(g, u, partial, ticket, T_end, dt, time,
+                                                                              status);
   });
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_dt_final(partial, nblk, g.hx, g.hy, 1, g.cfl, T_end, dt, time, st);
+  return cudaGetLastError();
 }
 
 // One block per SM: a 1D step is latency-bound and the FP64 pipe of an SM is

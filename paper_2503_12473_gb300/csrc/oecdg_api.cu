@@ -118,7 +118,7 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
     ALLOC(buf_d, c->numel * sizeof(double));
   }
   ALLOC(partials, (size_t)2 * c->nblk * c->F * 3 * sizeof(double));
-  ALLOC(wave_partial, (size_t)c->wave_blk * 2 * sizeof(double));
+  ALLOC(wave_partial, ((size_t)c->wave_blk * 2 + 1) * sizeof(double));  // + the 1D time step's ticket
   ALLOC(dt, 2 * sizeof(double));
   ALLOC(rhs_dt, 2 * sizeof(double));
   ALLOC(time, 2 * sizeof(double));
@@ -130,6 +130,8 @@ cdg_status cdg_init_mesh(const cdg_mesh_desc* desc, void* stream, cdg_ctx** out)
   e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->time, 0, sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, 2 * sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->wave_partial + 2 * (size_t)c->wave_blk, 0, sizeof(double), c->stream);
   // the scratch states start at 0, so that the primal mesh's unused slots of
   // the padded layout (walls) stay 0 through every stage and copy
   if (e == cudaSuccess) e = cudaMemsetAsync(c->buf_a, 0, c->numel * sizeof(double), c->stream);
@@ -260,8 +262,17 @@ static StageComb comb2(const double* u0, double c0, const double* u1, double c1,
   return cb;
 }
 
-// sigma from the partials of the last stage kernel, then the OE kernel
+// sigma from the partials of the last stage kernel, then the OE kernel (1D:
+// both in one launch)
 static cudaError_t run_oe(cdg_ctx* ctx, const double* uh, double* usig, double* delta) {
+  if (ctx->d.dim == 1) {
+    ctx->launches += 1;
+    prof_mark(ctx, PROF_OE, 0);
+    cudaError_t e = launch_oe1d_sig(ctx->sys, ctx->bc, ctx->d.k, ctx->g, uh, usig, ctx->dt, ctx->partials, ctx->nblk,
+                                    ctx->sn, ctx->sigma, ctx->avg, delta, ctx->status, ctx->stream);
+    prof_mark(ctx, PROF_OE, 1);
+    return e;
+  }
   cudaError_t e = launch_sigma(ctx->partials, ctx->nblk, ctx->F, ctx->sn, ctx->sigma, ctx->avg, ctx->stream);
   if (e != cudaSuccess) return e;
   ctx->launches += 2;
@@ -289,7 +300,7 @@ cdg_status cdg_rhs(cdg_ctx* ctx, const double* d_u, double tau_max, double* d_L)
 }
 
 static cudaError_t launch_dt(cdg_ctx* ctx, const double* d_u, double T_end) {
-  ctx->launches += 2;
+  ctx->launches += ctx->d.dim == 1 ? 1 : 2;  // 1D: the last block sets tau
   if (ctx->gen2)
     return launch_dt2k(ctx->sys, ctx->d.k, basis_of(ctx), ctx->g, d_u, ctx->wave_partial, ctx->wave_blk, T_end,
                        ctx->dt, ctx->time, ctx->status, ctx->stream);
@@ -477,6 +488,7 @@ cdg_status cdg_step_graph(cdg_ctx* ctx, double* d_u, double t, double T_end, int
     cudaError_t e2 = e == cudaSuccess ? enqueue_step(ctx, d_u, T_end) : e;
     if (e == cudaSuccess) e = cudaStreamEndCapture(ctx->stream, &graph);
     ctx->capturing = 0;
+    const long long per_step = ctx->launches - l0;  // the kernels of one captured step
     ctx->launches = l0;
     if (e2 != cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
@@ -487,12 +499,7 @@ cdg_status cdg_step_graph(cdg_ctx* ctx, double* d_u, double t, double T_end, int
     }
     ctx->graph_u = d_u;
     ctx->graph_tend = T_end;
-    ctx->graph_launches = 0;
-    {
-      // count the kernels of one step (the same launches as enqueue_step)
-      const int nst = n_stages(ctx->d.rk);
-      ctx->graph_launches = 2 + (long long)nst * (1 + (ctx->d.oe ? 2 : 0));
-    }
+    ctx->graph_launches = per_step;
   }
   CK(launch_set2(ctx->time, t, 0.0, ctx->stream), "step_graph");
   ctx->launches += 1;

@@ -34,6 +34,10 @@ cudaError_t launch_stage1d(int sys, int bc, int k, const Geo& g, int rhs_only, c
                            const StageComb& cb, double* out, const double* dt, double* partials, cudaStream_t st);
 cudaError_t launch_oe1d(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
                         const double* sigma, double* delta, int* status, cudaStream_t st);
+// sigma from the stage partials and the OE step in one launch (1D)
+cudaError_t launch_oe1d_sig(int sys, int bc, int k, const Geo& g, const double* uh, double* usig, const double* dt,
+                            const double* partials, long long nblk, const SigmaNorm& sn, double* sigma, double* avg,
+                            double* delta, int* status, cudaStream_t st);
 cudaError_t launch_dt1d(int sys, int k, const Geo& g, const double* u, double* partial, int nblk, double T_end,
                         double* dt, double* time, int* status, cudaStream_t st);
 cudaError_t launch_points1d(int k, const Geo& g, double ax, double bx, double* x, cudaStream_t st);
