@@ -74,20 +74,39 @@ struct RhsAcc {
 
 template <int SYS, int BC, int LD, class Acc>
 __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restrict__ u, int mesh, int i, int j,
-                                           double inv_tm, Acc& R) {
+                                           const double* stc, Acc& R) {
   constexpr int F = Fields<SYS>::F;
   const long long P = g.plane;
   const double* uo = u + (long long)(1 - mesh) * F * 9 * P;
   const int off = mesh == 0 ? -1 : 0;
-  const double kd = 0.5 * g.hy * inv_tm;  // dissipation scale inside A
+  // stc: the caller's shared step constants, stc[0] = 1/tau_max, written by
+  // thread 32 before this function's barrier (read only after it)
   // the dissipation weights w_qy kd P_b(eta) (b = 0, 1, 2) of every point row,
   // uniform over the block: computed once into shared memory, so the points
   // take them by broadcast instead of scaling every field value by kd
+  // likewise the column weights of the x-projection (wa, wa P_1, wa P_2, wb,
+  // wb P_2' per (sx, qx), with wa = w_qx 2/hy, wb = w_qx 2/hx) and the x-face
+  // scale 4/hx: the same quotients and products, taken once per block
   __shared__ double wk[2][3][3];
+  __shared__ double wc[2][3][5];
+  __shared__ double wf;
+  __syncthreads();  // stc
   if (threadIdx.x < 18) {
+    const double kd = 0.5 * g.hy * stc[0];  // dissipation scale inside A
     const int sy = threadIdx.x / 9, qy = (threadIdx.x / 3) % 3, c = threadIdx.x % 3;
     const double es = xs_self(sy, qy);
     wk[sy][qy][c] = gwt(qy) * (c == 0 ? 1.0 : (c == 1 ? es : lp(2, es))) * kd;
+  } else if (threadIdx.x < 24) {
+    const int sx = (threadIdx.x - 18) / 3, qx = (threadIdx.x - 18) % 3;
+    const double xsf = xs_self(sx, qx);
+    const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
+    wc[sx][qx][0] = wa;
+    wc[sx][qx][1] = wa * xsf;
+    wc[sx][qx][2] = wa * lp(2, xsf);
+    wc[sx][qx][3] = wb;
+    wc[sx][qx][4] = wb * dlp(2, xsf);
+  } else if (threadIdx.x == 24) {
+    wf = 4.0 / g.hx;
   }
   __syncthreads();
   R.zero();
@@ -138,7 +157,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
       }
       // R += (-s) P_a(s) (4/hx) Bf, s = 2 sx - 1 (explicit fma: one rounding
       // per update, the same in every kernel that inlines this)
-      const double sc = 4.0 / g.hx, sp = sx ? -sc : sc;
+      const double sc = wf, sp = sx ? -sc : sc;
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -151,7 +170,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
     // ---- the three volume columns of this half
 #pragma unroll
     for (int qx = 0; qx < 3; ++qx) {
-      const double xo = xs_other(sx, qx), xsf = xs_self(sx, qx);
+      const double xo = xs_other(sx, qx);
       double A[F][3], B[F][3];
 #pragma unroll
       for (int f = 0; f < F; ++f)
@@ -209,8 +228,8 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
         }
       }
       // R += w_qx [ P_a(xi) (2/hy) A + P'_a(xi) (2/hx) B ]
-      const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
-      const double wa1 = wa * xsf, wa2 = wa * lp(2, xsf), wb2 = wb * dlp(2, xsf);
+      const double wa = wc[sx][qx][0], wa1 = wc[sx][qx][1], wa2 = wc[sx][qx][2];
+      const double wb = wc[sx][qx][3], wb2 = wc[sx][qx][4];
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -281,10 +300,23 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
   constexpr int F = Fields<SYS>::F;
   const bool active = i < g.nx && j < g.ny;
   const int ic = active ? i : 0, jc = active ? j : 0;
-  const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
-  const double inv_tm = 1.0 / tm;
+  // the step's constants, once per block: 1/tau_max and the combination's
+  // cb alpha, cb tau (below); the barrier in cell_rhs2d publishes them
+  __shared__ double stc[3];
+  if (threadIdx.x == 32) {
+    const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
+    stc[0] = 1.0 / tm;
+    // u_out = ca u^n + cb (u_in + tau L(u_in)) with L = c_ab R - u_in / tau_max
+    //       = ca u^n + cb alpha u_in + cb tau c_ab R,   alpha = 1 - tau / tau_max:
+    // alpha = 0 unless the step is clipped at the end time, and then the cell's
+    // own coefficients drop out (the two u_in terms cancel exactly).
+    const double alpha = tau == tm ? 0.0 : (tm - tau) / tm;
+    stc[1] = cb * alpha;
+    stc[2] = cb * tau;
+  }
   RhsAcc<F> R;
-  cell_rhs2d<SYS, BC, LD>(g, uin, mesh, ic, jc, inv_tm, R);
+  cell_rhs2d<SYS, BC, LD>(g, uin, mesh, ic, jc, stc, R);
+  const double inv_tm = stc[0];
   const long long P = g.plane;
   const long long base = (long long)mesh * F * 9 * P + (long long)jc * g.nx + ic;
   if (MODE == MODE_RHS) {
@@ -297,12 +329,7 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
                                             -inv_tm * ldv<LD>(uin + base + (f * 9 + m) * P));
     return;
   } else {
-    // u_out = ca u^n + cb (u_in + tau L(u_in)) with L = c_ab R - u_in / tau_max
-    //       = ca u^n + cb alpha u_in + cb tau c_ab R,   alpha = 1 - tau / tau_max:
-    // alpha = 0 unless the step is clipped at the end time, and then the cell's
-    // own coefficients drop out (the two u_in terms cancel exactly).
-    const double alpha = tau == tm ? 0.0 : (tm - tau) / tm;
-    const double cba = cb * alpha, cbt = cb * tau;
+    const double cba = stc[1], cbt = stc[2];
     __shared__ double sh[96];
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -316,21 +343,27 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
         v[m] = s;
         if (active) out[id] = s;
       }
-      // values at the cell's own 3x3 Gauss points: x-contraction then y; their
-      // extrema as integer keys
+      // values at the cell's own 3x3 Gauss points, y-contraction then x; their
+      // extrema as integer keys.  The 3-point nodes are 0 and +-g, so along
+      // each direction c0 + c1 P_1 + c2 P_2 takes c0 - c2/2 at 0 and
+      // (c0 + P_2(g) c2) +- g c1 at +-g: 4 FMA for the 3 points, not 6.
       long long kx = LLONG_MIN, kn = LLONG_MAX;
+      constexpr double G = gnode(2), P2G = lp(2, gnode(2));
+      double t[3][3];  // [node of eta: -g, 0, +g][a]
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double e = fma(P2G, v[6 + a], v[a]);
+        t[0][a] = fma(-G, v[3 + a], e);
+        t[1][a] = fma(-0.5, v[6 + a], v[a]);
+        t[2][a] = fma(G, v[3 + a], e);
+      }
 #pragma unroll
       for (int qy = 0; qy < 3; ++qy) {
-        double t[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          t[a] = fma(lp(2, gnode(qy)), v[6 + a], fma(gnode(qy), v[3 + a], v[a]));
-#pragma unroll
-        for (int qx = 0; qx < 3; ++qx) {
-          const long long k = dkey(fma(lp(2, gnode(qx)), t[2], fma(gnode(qx), t[1], t[0])));
-          kx = max(kx, k);
-          kn = min(kn, k);
-        }
+        const double e = fma(P2G, t[qy][2], t[qy][0]);
+        const long long k0 = dkey(fma(-G, t[qy][1], e)), k1 = dkey(fma(-0.5, t[qy][2], t[qy][0]));
+        const long long k2 = dkey(fma(G, t[qy][1], e));
+        kx = max(kx, max(k0, max(k1, k2)));
+        kn = min(kn, min(k0, min(k1, k2)));
       }
       double s = active ? v[0] : 0.0;
       if (!active) {
