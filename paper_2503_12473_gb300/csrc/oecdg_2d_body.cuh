@@ -84,29 +84,13 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
   // the dissipation weights w_qy kd P_b(eta) (b = 0, 1, 2) of every point row,
   // uniform over the block: computed once into shared memory, so the points
   // take them by broadcast instead of scaling every field value by kd
-  // likewise the column weights of the x-projection (wa, wa P_1, wa P_2, wb,
-  // wb P_2' per (sx, qx), with wa = w_qx 2/hy, wb = w_qx 2/hx) and the x-face
-  // scale 4/hx: the same quotients and products, taken once per block
   __shared__ double wk[2][3][3];
-  __shared__ double wc[2][3][5];
-  __shared__ double wf;
   __syncthreads();  // stc
   if (threadIdx.x < 18) {
     const double kd = 0.5 * g.hy * stc[0];  // dissipation scale inside A
     const int sy = threadIdx.x / 9, qy = (threadIdx.x / 3) % 3, c = threadIdx.x % 3;
     const double es = xs_self(sy, qy);
     wk[sy][qy][c] = gwt(qy) * (c == 0 ? 1.0 : (c == 1 ? es : lp(2, es))) * kd;
-  } else if (threadIdx.x < 24) {
-    const int sx = (threadIdx.x - 18) / 3, qx = (threadIdx.x - 18) % 3;
-    const double xsf = xs_self(sx, qx);
-    const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
-    wc[sx][qx][0] = wa;
-    wc[sx][qx][1] = wa * xsf;
-    wc[sx][qx][2] = wa * lp(2, xsf);
-    wc[sx][qx][3] = wb;
-    wc[sx][qx][4] = wb * dlp(2, xsf);
-  } else if (threadIdx.x == 24) {
-    wf = 4.0 / g.hx;
   }
   __syncthreads();
   R.zero();
@@ -157,7 +141,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
       }
       // R += (-s) P_a(s) (4/hx) Bf, s = 2 sx - 1 (explicit fma: one rounding
       // per update, the same in every kernel that inlines this)
-      const double sc = wf, sp = sx ? -sc : sc;
+      const double sc = 4.0 / g.hx, sp = sx ? -sc : sc;
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -170,7 +154,7 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
     // ---- the three volume columns of this half
 #pragma unroll
     for (int qx = 0; qx < 3; ++qx) {
-      const double xo = xs_other(sx, qx);
+      const double xo = xs_other(sx, qx), xsf = xs_self(sx, qx);
       double A[F][3], B[F][3];
 #pragma unroll
       for (int f = 0; f < F; ++f)
@@ -228,8 +212,10 @@ __device__ __forceinline__ void cell_rhs2d(const Geo& g, const double* __restric
         }
       }
       // R += w_qx [ P_a(xi) (2/hy) A + P'_a(xi) (2/hx) B ]
-      const double wa = wc[sx][qx][0], wa1 = wc[sx][qx][1], wa2 = wc[sx][qx][2];
-      const double wb = wc[sx][qx][3], wb2 = wc[sx][qx][4];
+      // (taking these per-block constants from shared memory instead moved
+      // register spills out to DRAM and lengthened the kernel)
+      const double wa = gwt(qx) * 2.0 / g.hy, wb = gwt(qx) * 2.0 / g.hx;
+      const double wa1 = wa * xsf, wa2 = wa * lp(2, xsf), wb2 = wb * dlp(2, xsf);
 #pragma unroll
       for (int f = 0; f < F; ++f)
 #pragma unroll
