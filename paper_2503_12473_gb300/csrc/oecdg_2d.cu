@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(NT, OECDG_OE_MINB) k_oe2d(Geo g, const double*
                                              const double* __restrict__ dt, const double* __restrict__ sigma,
                                              double* __restrict__ delta_out, int* __restrict__ status) {
   __shared__ double isg[Fields<SYS>::F];
+  __shared__ double osh[2 * TY * TX * OSER_N];  // the rows' shared y-face series
   oe_inv_sigma<Fields<SYS>::F>(sigma, blockIdx.x & 1, isg);
-  oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.x & 1,
-                                          (blockIdx.x >> 1) * TX + (threadIdx.x % TX),
-                                          blockIdx.y * TY + (threadIdx.x / TX), nullptr, isg);
+  oe_cell2d<SYS, BC, WRITE_DELTA, 0, ISO, LD_NC, TY>(g, uh, usig, dt, sigma, delta_out, status, blockIdx.x & 1,
+                                                     (blockIdx.x >> 1) * TX + (threadIdx.x % TX),
+                                                     blockIdx.y * TY + (threadIdx.x / TX), nullptr, isg, osh,
+                                                     threadIdx.x / TX);
 }
 
 // ------------------------------------------------------------- time step --

@@ -374,14 +374,76 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 // ISO = true requires hx == hy: every m-th derivative then carries the same
 // factor (2/h)^m, so the traces stay in reference units and the factor is
 // applied once, in the constants of delta^m (the recorded sums are physical).
-template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false, int LD = LD_NC>
+// The overlapping cell's part of one half-face's difference series: its
+// trace at its centre line (normal coordinate 0) re-expanded in K's
+// tangential coordinate (shift dl): for each series X (value o0, first normal
+// derivative o1, second / 3 o2), X_2, the P_1 coefficient fma(3 dl, X_2, X_1)
+// and the P_0 coefficient fma(3/2, X_2, fma(dl, X_1, X_0)), plus o2's raw
+// first two coefficients.  It depends on the overlapping cell and dl only, so
+// the two cells on either side of a face (cells j and j + 1 for a face normal
+// to y) can share it.
+struct OSer {
+  double o02, E01, E00, o12, E11, E10, o22, E21, E20, o20, o21;
+};
+constexpr int OSER_N = 11;
+
+template <int LD, bool ISO>
+__device__ __forceinline__ OSer oe_oseries(const double* co, long long P, int n, double dl) {
+  double w0[3], w1[3], w2[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    w0[t] = ldv<LD>(co + (n == 0 ? t * 3 : t) * P);
+    w1[t] = ldv<LD>(co + (n == 0 ? t * 3 + 1 : 3 + t) * P);
+    w2[t] = ldv<LD>(co + (n == 0 ? t * 3 + 2 : 6 + t) * P);
+  }
+  const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
+  OSer s;
+  s.o02 = o0[2];
+  s.E01 = fma(3.0 * dl, o0[2], o0[1]);
+  s.E00 = fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
+  s.o12 = w1[2];
+  s.E11 = fma(3.0 * dl, w1[2], w1[1]);
+  s.E10 = fma(1.5, w1[2], fma(dl, w1[1], w1[0]));
+  s.o22 = w2[2];
+  s.E21 = fma(3.0 * dl, w2[2], w2[1]);
+  s.E20 = ISO ? 0.0 : fma(1.5, w2[2], fma(dl, w2[1], w2[0]));
+  s.o20 = w2[0];
+  s.o21 = w2[1];
+  return s;
+}
+
+__device__ __forceinline__ void oser_store(double* p, const OSer& s) {
+  p[0] = s.o02; p[1] = s.E01; p[2] = s.E00; p[3] = s.o12; p[4] = s.E11; p[5] = s.E10;
+  p[6] = s.o22; p[7] = s.E21; p[8] = s.E20; p[9] = s.o20; p[10] = s.o21;
+}
+__device__ __forceinline__ OSer oser_load(const double* p) {
+  OSer s;
+  s.o02 = p[0]; s.E01 = p[1]; s.E00 = p[2]; s.o12 = p[3]; s.E11 = p[4]; s.E10 = p[5];
+  s.o22 = p[6]; s.E21 = p[7]; s.E20 = p[8]; s.o20 = p[9]; s.o21 = p[10];
+  return s;
+}
+
+// ROWS > 0: the block is ROWS rows of 32 cells (row ty = warp ty, cell i of
+// lane i % 32), and the rows share the faces between them: for each field,
+// every cell first takes the overlapping-cell series of its upper y-face
+// (both halves) into osh[2][ROWS][32][OSER_N] (shared), and after a barrier a
+// cell above row 0 reads its lower face's series from the row below instead
+// of loading and forming it.  The arithmetic is the same, so the results are
+// the same bits as with ROWS = 0.  Every thread of the block must call it (no
+// early return: a cell outside the mesh computes a clamped cell and stores
+// nothing).
+template <int SYS, int BC, bool WRITE_DELTA, int REC = 0, bool ISO = false, int LD = LD_NC, int ROWS = 0>
 __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict__ uh, double* __restrict__ usig,
                                           const double* __restrict__ dt, const double* __restrict__ sigma,
                                           double* __restrict__ delta_out, int* __restrict__ status, int mesh, int i,
                                           int j, double* __restrict__ rec = nullptr,
-                                          const double* __restrict__ isg = nullptr) {
+                                          const double* __restrict__ isg = nullptr, double* osh = nullptr,
+                                          int ty = 0) {
   constexpr int F = Fields<SYS>::F;
-  if (i >= g.nx || j >= g.ny) return;
+  const bool active = i < g.nx && j < g.ny;
+  if (ROWS == 0 && !active) return;
+  if (!active) i = j = 0;
+  const int lane = threadIdx.x & 31;
   const long long P = g.plane;
   const double* us = uh + (long long)mesh * F * 9 * P + (long long)j * g.nx + i;
   const double* uo = uh + (long long)(1 - mesh) * F * 9 * P;
@@ -399,7 +461,7 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     double c = 0.0;
     if (rho > 0.0 && p > 0.0) {
       c = sqrt_pos(fma(g.gamma * p, r, SQ_FLOOR));
-    } else {
+    } else if (active) {
       atomicOr(status, ST_NONPHYSICAL);
     }
     bx = fabs(vx) + c;
@@ -427,6 +489,14 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
     double u[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) u[m] = ldv<LD>(cs + m * P);
+    if (ROWS > 0) {  // this cell's upper y-face, both halves, for itself and the row above
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double* co = uo + f * 9 * P + (long long)oj1 * g.nx + (h ? oi1 : oi0);
+        oser_store(osh + ((h * ROWS + ty) * 32 + lane) * OSER_N, oe_oseries<LD, ISO>(co, P, 1, 1.0 - 2.0 * h));
+      }
+      __syncthreads();
+    }
     double Sx0 = 0.0, Sx1 = 0.0, Sx2 = 0.0, Sy0 = 0.0, Sy1 = 0.0, Sy2 = 0.0;
     // Faces normal to direction n (0: x, 1: y), at reference coordinate s of K.
     // Along the face, K's trace and its normal derivatives of order 0, 1, 2 are
@@ -472,30 +542,28 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const double dl = 1.0 - 2.0 * h;
-          const int oi = n == 0 ? (side ? oi1 : oi0) : (h ? oi1 : oi0);
-          const int oj = n == 0 ? (h ? oj1 : oj0) : (side ? oj1 : oj0);
-          const double* co = uo + f * 9 * P + (long long)oj * g.nx + oi;
-          double w0[3], w1[3], w2[3];
-#pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            w0[t] = ldv<LD>(co + (n == 0 ? t * 3 : t) * P);
-            w1[t] = ldv<LD>(co + (n == 0 ? t * 3 + 1 : 3 + t) * P);
-            w2[t] = ldv<LD>(co + (n == 0 ? t * 3 + 2 : 6 + t) * P);
+          // the overlapping cell's series: shared with the row below / above
+          // where ROWS > 0, else formed here
+          OSer o;
+          if (ROWS > 0 && n == 1 && side == 1) {
+            o = oser_load(osh + ((h * ROWS + ty) * 32 + lane) * OSER_N);
+          } else if (ROWS > 0 && n == 1 && side == 0 && ty > 0) {
+            o = oser_load(osh + ((h * ROWS + ty - 1) * 32 + lane) * OSER_N);
+          } else {
+            const int oi = n == 0 ? (side ? oi1 : oi0) : (h ? oi1 : oi0);
+            const int oj = n == 0 ? (h ? oj1 : oj0) : (side ? oj1 : oj0);
+            o = oe_oseries<LD, ISO>(uo + f * 9 * P + (long long)oj * g.nx + oi, P, n, dl);
           }
-          // overlapping trace at its centre line (normal coordinate 0)
-          const double o0[3] = {fma(-0.5, w2[0], w0[0]), fma(-0.5, w2[1], w0[1]), fma(-0.5, w2[2], w0[2])};
-          const double* o1 = w1;
-          const double* o2 = w2;  // (second normal derivative) / 3
           // difference series in K's tangential coordinate (e0_2 as 3 e0_2)
           double e0[2], e1[3], e2[3];
-          const double e02x3 = fma(-3.0, o0[2], c0x3);
-          e0[1] = c0[1] - fma(3.0 * dl, o0[2], o0[1]);
-          e0[0] = c0[0] - fma(1.5, o0[2], fma(dl, o0[1], o0[0]));
-          e1[2] = c1[2] - o1[2];
-          e1[1] = c1[1] - fma(3.0 * dl, o1[2], o1[1]);
-          e1[0] = c1[0] - fma(1.5, o1[2], fma(dl, o1[1], o1[0]));
-          e2[2] = c2[2] - o2[2];
-          e2[1] = c2[1] - fma(3.0 * dl, o2[2], o2[1]);
+          const double e02x3 = fma(-3.0, o.o02, c0x3);
+          e0[1] = c0[1] - o.E01;
+          e0[0] = c0[0] - o.E00;
+          e1[2] = c1[2] - o.o12;
+          e1[1] = c1[1] - o.E11;
+          e1[0] = c1[0] - o.E10;
+          e2[2] = c2[2] - o.o22;
+          e2[1] = c2[1] - o.E21;
           // physical scalings: normal derivative series (order 1, 2), tangential
           // derivative of the value and of the normal derivative, second
           // tangential derivative (a constant on the half-face)
@@ -504,14 +572,14 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
           // go into the points' constant coefficients, see hn and hm below)
           if constexpr (ISO) {
             a0 = e1[0], a1 = e1[1], a2 = e1[2];
-            b0 = fma(-4.5, o2[2], fma(-3.0 * dl, o2[1], fma(-3.0, o2[0], k2x3)));  // 3 e2_0
+            b0 = fma(-4.5, o.o22, fma(-3.0 * dl, o.o21, fma(-3.0, o.o20, k2x3)));  // 3 e2_0
             b1 = e2[1], b2 = e2[2];
             t0 = e0[1], t1 = e02x3;
             m0 = a1, m1 = a2;
             tt = t1;
           } else {
             const double dn2x3 = 3.0 * dn2;
-            e2[0] = c2[0] - fma(1.5, o2[2], fma(dl, o2[1], o2[0]));
+            e2[0] = c2[0] - o.E20;
             a0 = dn1 * e1[0], a1 = dn1 * e1[1], a2 = dn1 * e1[2];
             b0 = dn2x3 * e2[0], b1 = dn2x3 * e2[1], b2 = dn2x3 * e2[2];
             t0 = dt1 * e0[1], t1 = dt1 * e02x3;
@@ -552,7 +620,9 @@ __device__ __forceinline__ void oe_cell2d(const Geo& g, const double* __restrict
         d2 = fmax(d2, v2);
       }
     }
+    if (ROWS > 0) __syncthreads();  // osh is rewritten for the next field
   }
+  if (!active) return;
   if (REC) {
     double* r = rec + ((long long)mesh * P + (long long)j * g.nx + i) * 12;
     const double dd[3] = {d0, d1, d2};

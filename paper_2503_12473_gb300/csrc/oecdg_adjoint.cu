@@ -514,10 +514,12 @@ __global__ void __launch_bounds__(AT) k_oe_rec2d(Geo g, const double* __restrict
                                                  const double* __restrict__ dt, const double* __restrict__ sigma,
                                                  int* __restrict__ status, double* __restrict__ rec) {
   __shared__ double isg[Fields<SYS>::F];
+  __shared__ double osh[2 * (AT / 32) * 32 * OSER_N];  // the rows' shared y-face series
   oe_inv_sigma<Fields<SYS>::F>(sigma, blockIdx.z, isg);
-  oe_cell2d<SYS, BC_PERIODIC, false, 1, ISO>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
-                                         blockIdx.x * 32 + (threadIdx.x & 31),
-                                         blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec, isg);
+  oe_cell2d<SYS, BC_PERIODIC, false, 1, ISO, LD_NC, AT / 32>(g, uh, usig, dt, sigma, nullptr, status, blockIdx.z,
+                                                            blockIdx.x * 32 + (threadIdx.x & 31),
+                                                            blockIdx.y * (AT / 32) + (threadIdx.x >> 5), rec, isg, osh,
+                                                            threadIdx.x >> 5);
 }
 
 // Reverse of one derivative order M of the face sums of one field: given the

@@ -82,14 +82,15 @@ __global__ void __launch_bounds__(32 * R) k_boe(const BatchInst* __restrict__ I,
   const int i = (t % in.tx) * 32 + (threadIdx.x & 31);
   const int j = (t / in.tx) * R + (threadIdx.x >> 5);
   __shared__ double isg[Fields<SYS>::F];
+  __shared__ double osh[2 * R * 32 * OSER_N];  // the rows' shared y-face series
   oe_inv_sigma<Fields<SYS>::F>(in.sigma, mesh, isg);
   // square cells: the isotropic variant, as the single-mesh launch chooses it
   if (in.g.hx == in.g.hy)
-    oe_cell2d<SYS, BC, false, 0, true>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j,
-                                       nullptr, isg);
+    oe_cell2d<SYS, BC, false, 0, true, LD_NC, R>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status,
+                                                 mesh, i, j, nullptr, isg, osh, threadIdx.x >> 5);
   else
-    oe_cell2d<SYS, BC, false>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status, mesh, i, j, nullptr,
-                              isg);
+    oe_cell2d<SYS, BC, false, 0, false, LD_NC, R>(in.g, in.a, last ? in.u : in.b, in.dt, in.sigma, nullptr, status,
+                                                  mesh, i, j, nullptr, isg, osh, threadIdx.x >> 5);
 }
 
 // avg and sigma per instance, mesh and field: grid (F, 2, n), one warp each,
@@ -195,6 +196,7 @@ template <int SYS, int BC, int R>
 __global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
   constexpr int F = Fields<SYS>::F;
   __shared__ double isg[F];  // 1/sigma of the OE phase's current tile (its instance and mesh)
+  __shared__ double osh[2 * R * 32 * OSER_N];  // the OE rows' shared y-face series
   const long long nwave = (long long)a.n * WB;
   for (int s = 0; s < a.nsteps; ++s) {
     for (long long it = blockIdx.x; it < nwave; it += gridDim.x)
@@ -234,11 +236,11 @@ __global__ void __launch_bounds__(32 * R) k_bpersist(BPersistArgs a) {
         __syncthreads();  // the previous tile's readers of isg are done
         oe_inv_sigma<F>(in.sigma, mesh, isg);
         if (in.g.hx == in.g.hy)
-          oe_cell2d<SYS, BC, false, 0, true, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i, j,
-                                                    nullptr, isg);
+          oe_cell2d<SYS, BC, false, 0, true, LD_CA, R>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i,
+                                                       j, nullptr, isg, osh, threadIdx.x >> 5);
         else
-          oe_cell2d<SYS, BC, false, 0, false, LD_CA>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i,
-                                                     j, nullptr, isg);
+          oe_cell2d<SYS, BC, false, 0, false, LD_CA, R>(in.g, in.a, out, in.dt, in.sigma, nullptr, a.status, mesh, i,
+                                                        j, nullptr, isg, osh, threadIdx.x >> 5);
       }
       if (!grid_sync(a.bar, a.expected, a.status, a.limit_ns)) return;
     }
