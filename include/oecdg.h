@@ -171,7 +171,10 @@ cdg_status cdg_rk_combine(cdg_ctx* ctx, const double* d_ul, int n, const double*
                           double ct, double* d_out);
 
 /* The OE step u_sigma = F_tau u_h (Eq. (OEstep2D), solved exactly): sigma_K
- * and avg per mesh and field, the damping coefficients delta_K^m (m = 0..k)
+ * and avg per mesh and field (sigma = the max over every cell's Gauss points
+ * of |u - avg|, taken as 0 when it is at most 2^-40 of the field's largest
+ * |u| there: a field constant up to rounding, whose delta is then 0 as for an
+ * exactly constant one), the damping coefficients delta_K^m (m = 0..k)
  * from the traces of u^C - u^D on the half-faces of every cell, the wave speed
  * beta_{e,K} at the cell average, and the exponential decay of every mode of
  * total degree >= 1.  tau from the context.  d_usig must not alias d_uh.
