@@ -84,13 +84,10 @@ __global__ void k_wave2d(Geo g, const double* __restrict__ u, double* __restrict
     const long long cell = c - mesh * g.plane;
     const double* us = u + (long long)mesh * F * 9 * g.plane + cell;
     if (SYS == SYS_EULER) {
-      const double rho = us[0], m1 = us[9 * g.plane], m2 = us[18 * g.plane], E = us[27 * g.plane];
-      const double vx = m1 / rho, vy = m2 / rho;
-      const double p = (g.gamma - 1.0) * fma(-0.5, fma(m1, vx, m2 * vy), E);
-      if (rho > 0.0 && p > 0.0) {
-        const double cs = sqrt(g.gamma * p / rho);
-        mx = fmax(mx, fabs(vx) + cs);
-        my = fmax(my, fabs(vy) + cs);
+      double bx, by;
+      if (euler2_wave(g.gamma, us[0], us[9 * g.plane], us[18 * g.plane], us[27 * g.plane], bx, by)) {
+        mx = fmax(mx, bx);
+        my = fmax(my, by);
       } else {
         atomicOr(status, ST_NONPHYSICAL);
       }

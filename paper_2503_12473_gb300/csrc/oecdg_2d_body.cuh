@@ -287,8 +287,9 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
   const bool active = i < g.nx && j < g.ny;
   const int ic = active ? i : 0, jc = active ? j : 0;
   // the step's constants, once per block: 1/tau_max and the combination's
-  // cb alpha, cb tau (below); the barrier in cell_rhs2d publishes them
-  __shared__ double stc[3];
+  // cb alpha, cb tau and cb tau c_ab (below); the barrier in cell_rhs2d
+  // publishes them
+  __shared__ double stc[12];
   if (threadIdx.x == 32) {
     const double tau = ldv<LD>(dt), tm = ldv<LD>(dt + 1);
     stc[0] = 1.0 / tm;
@@ -299,6 +300,8 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
     const double alpha = tau == tm ? 0.0 : (tm - tau) / tm;
     stc[1] = cb * alpha;
     stc[2] = cb * tau;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) stc[3 + m] = stc[2] * ((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0);  // cb tau c_ab
   }
   RhsAcc<F> R;
   cell_rhs2d<SYS, BC, LD>(g, uin, mesh, ic, jc, stc, R);
@@ -315,7 +318,7 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
                                             -inv_tm * ldv<LD>(uin + base + (f * 9 + m) * P));
     return;
   } else {
-    const double cba = stc[1], cbt = stc[2];
+    const double cba = stc[1];
     __shared__ double sh[96];
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -323,7 +326,7 @@ __device__ __forceinline__ void stage_cell2d(const Geo& g, const double* __restr
 #pragma unroll
       for (int m = 0; m < 9; ++m) {
         const long long id = base + (f * 9 + m) * P;
-        double s = (cbt * ((2 * (m % 3) + 1) * (2 * (m / 3) + 1) / 16.0)) * R.at(f, m / 3, m % 3);
+        double s = stc[3 + m] * R.at(f, m / 3, m % 3);  // (cb tau c_ab) R
         if (cba != 0.0) s = fma(cba, ldv<LD>(uin + id), s);
         if (ca != 0.0) s = fma(ca, ldv<LD>(un + id), s);
         v[m] = s;

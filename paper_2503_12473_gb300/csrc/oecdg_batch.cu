@@ -115,14 +115,11 @@ __device__ __forceinline__ void bwave_chunk(const BatchInst& in, int ch, int* __
     const long long cell = c - mesh * g.plane;
     const double* us = in.u + (long long)mesh * F * 9 * g.plane + cell;
     if (SYS == SYS_EULER) {
-      const double rho = ldv<LD>(us), m1 = ldv<LD>(us + 9 * g.plane), m2 = ldv<LD>(us + 18 * g.plane),
-                   E = ldv<LD>(us + 27 * g.plane);
-      const double vx = m1 / rho, vy = m2 / rho;
-      const double p = (g.gamma - 1.0) * fma(-0.5, fma(m1, vx, m2 * vy), E);
-      if (rho > 0.0 && p > 0.0) {
-        const double cs = sqrt(g.gamma * p / rho);
-        mx = fmax(mx, fabs(vx) + cs);
-        my = fmax(my, fabs(vy) + cs);
+      double bx, by;
+      if (euler2_wave(g.gamma, ldv<LD>(us), ldv<LD>(us + 9 * g.plane), ldv<LD>(us + 18 * g.plane),
+                      ldv<LD>(us + 27 * g.plane), bx, by)) {
+        mx = fmax(mx, bx);
+        my = fmax(my, by);
       } else {
         atomicOr(status, ST_NONPHYSICAL);
       }

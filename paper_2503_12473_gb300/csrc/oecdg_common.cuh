@@ -254,6 +254,21 @@ struct Euler2 {
   }
 };
 
+// The 2D Euler wave speeds |u| + c and |v| + c at a cell average (rho, m1,
+// m2, E) for the time step, with the seeded reciprocal and square root (the
+// OE kernel's beta takes the same formula); false for a non-physical state.
+__device__ __forceinline__ bool euler2_wave(double gamma, double rho, double m1, double m2, double E, double& bx,
+                                            double& by) {
+  const double r = rcp_pos(rho);  // NaN for rho <= 0 or subnormal: rejected below
+  const double vx = m1 * r, vy = m2 * r;
+  const double p = (gamma - 1.0) * fma(-0.5, fma(m1, vx, m2 * vy), E);
+  if (!(rho > 0.0 && p > 0.0)) return false;
+  const double c = sqrt_pos(fma(gamma * p, r, SQ_FLOOR));
+  bx = fabs(vx) + c;
+  by = fabs(vy) + c;
+  return true;
+}
+
 // Block-level reductions (sum, max, min) over blockDim.x threads (a multiple
 // of 32, at most 1024).  `sh` holds 3 * 32 doubles.  Result valid in thread 0.
 __device__ __forceinline__ void block_reduce3(double& s, double& mx, double& mn, double* sh) {
