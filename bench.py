@@ -46,14 +46,14 @@ HBM_FALLBACK_GBS = 6800.0
 # the two hot kernels, counted from the executed FP64 instructions of one
 # launch (2 x DFMA + DADD + DMUL) divided by the cells of the launch: the
 # kernels are fully unrolled, so this is the arithmetic of the algorithm as
-# implemented.  The stage kernel's first stage (no u^n term) does 6,905 per
-# cell, the other two 6,977: the figure is their mean over a step.  Source: an
+# implemented.  The stage kernel's first stage (no u^n term) does 6,899 per
+# cell, the other two 6,971: the figure is their mean over a step.  Source: an
 # ncu capture of the FP64 instruction counters of the three stage and three OE
 # launches of one 512^2 step.
-FLOPS_PER_CELL = {"stage": 6953, "oe": 5808}
+FLOPS_PER_CELL = {"stage": 6947, "oe": 5808}
 # DRAM bytes per cell per launch (ncu dram__bytes_read + write, same capture,
 # mean over the step's launches); None once a kernel changes after the capture.
-TRAFFIC_PER_CELL = {"stage": 831, "oe": 501}
+TRAFFIC_PER_CELL = {"stage": 828, "oe": 501}
 # Algorithmic HBM bytes per cell: stage reads u_in (36 doubles) and, in two of
 # three stages, u^n (36), writes u_h (36); OE reads u_h (36), writes u_sigma (36)
 # (neighbour re-reads, of both meshes, are L2 hits: the two meshes' blocks of a
