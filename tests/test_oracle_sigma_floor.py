@@ -11,8 +11,13 @@ after the projection, and its computed sigma is then a few ulps too.
 Checked here: sigma against the plain definition, evaluated independently from
 the point values (orc_eval_cells) and the cell-average mean; the floor on both
 sides of 2^-40; and that a rounding-noisy uniform density (Section 4's
-two-blast-wave start) steps like the exactly constant one.
+two-blast-wave start) steps like the exactly constant one.  Also the
+multi-index sum in delta^2 (each multi-index once), by a closed-form ratio
+that a multinomial (rotation-invariant) weighting of the mixed derivative
+fails.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -103,3 +108,36 @@ def test_rounding_noise_in_a_uniform_density_does_not_damp():
     b, *_ = O.advance(p, clean, 0.0, w.T, 1)
     rel = np.abs(a - b).max(axis=(0, 2, 3, 4)) / np.abs(b).max(axis=(0, 2, 3, 4))
     assert rel.max() < 1e-13, rel
+
+
+def _delta2_of_local_quadratic(coef):
+    """delta^2 of a primal cell of a periodic 4 x 4 Q^2 advection mesh whose
+    primal cells all hold the same local polynomial (modal coefficients coef
+    at (a, b), Q^2 index 3 b + a) plus a large linear part 1e6 P_1(xi), and
+    whose dual mesh is 0: u^C - u^D on every half-face is the cell's own
+    polynomial, sigma is set by the linear part (the same for every coef to
+    1e-6), and the second derivatives are constants."""
+    p = O.Problem(dim=2, nx=4, ny=4, k=2, basis=O.BASIS_Q, system=O.ADVECTION, bc=O.PERIODIC, adv_x=1.0,
+                  adv_y=1.0, cfl=0.1)
+    u = p.zeros()
+    u[0, 0, 1] = 1e6  # (a, b) = (1, 0)
+    for (a, b), c in coef.items():
+        u[0, 0, 3 * b + a] += c
+    delta, sigma, _, st = O.oe_coefficients(p, u)
+    assert st == O.OK
+    return delta[0, 1, 2, 2], sigma[0, 0]
+
+
+def test_delta2_is_the_plain_multi_index_sum():
+    """Section 2.2's delta^m integrates (sum over |alpha| = m of
+    (d^alpha (u^C - u^D))^2)^(1/2): for m = 2 the multi-indices (2,0), (1,1),
+    (0,2), each once.  A face integrand that is constant makes delta^2
+    proportional to that square root: xi eta (only the mixed derivative, 1)
+    against (xi^2 - eta^2)/2 = (P_2(xi) - P_2(eta))/3 (the pure ones, 1 and -1)
+    gives sqrt(1 / 2) -- the same rotated function, so a rotation-invariant
+    (multinomial, Frobenius) sum would give 1."""
+    d_mixed, s1 = _delta2_of_local_quadratic({(1, 1): 1.0})
+    d_pure, s2 = _delta2_of_local_quadratic({(2, 0): 1.0 / 3.0, (0, 2): -1.0 / 3.0})
+    assert abs(s1 / s2 - 1.0) < 1e-5
+    assert d_mixed > 0.0 and d_pure > 0.0
+    assert abs(d_mixed / d_pure - math.sqrt(0.5)) < 1e-5, d_mixed / d_pure
